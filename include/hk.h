@@ -1,0 +1,154 @@
+/*
+ * hk.h -- C ABI of libhk: the extended-precision Cholesky factorisation of a
+ * Hankel moment matrix and inverse iteration for its smallest eigenvalue, on
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * The operation (Emmart, Weems and Chen, "Computing the smallest eigenvalue of
+ * large ill-conditioned Hankel matrices"):
+ *   - the matrix is M_ij = m_{i+j}, i, j = 0..N-1, with the moments
+ *     m_k = Gamma((1+k)/beta)/beta of the weight exp(-x^beta) (Introduction,
+ *     definition of M; section "Hankel matrices, the moment problem ...");
+ *   - M = R^T R with R upper triangular: the submatrix-order LDL^T of section
+ *     "The LDL^T Determinant Algorithm" written as Cholesky (R = D^1/2 L^T);
+ *   - inverse iteration with two triangular solves per step, lambda_t the
+ *     inverse of the Rayleigh quotient of M^-1 (section "M is extremely
+ *     ill-conditioned" bounds the spectrum by the Rayleigh quotient).
+ *
+ * Number format (hk_mp): value = (-1)^sign * m * 2^exp with the mantissa
+ * m = sum_l limbs[l] * 2^(32 l), l = 0..L-1, L = P/32, normalised so that
+ * 2^(P-1) <= m < 2^P, or m = 0 (then sign = 0 and exp = 0).  P is a multiple
+ * of 32.  Exponents are 64-bit and never overflow in practice.
+ *
+ * Semantics, exactly as the CPU oracle computes them:
+ *   A_ij = m_{i+j} - sum_{t<i} R_ti R_tj       (exact, no rounding)
+ *   S_ij = RNE_P(A_ij);  S_ii <= 0 -> HK_ERR_NOT_PD
+ *   R_ii = RNE_P(sqrt(S_ii));  R_ij = RNE_P(S_ij / R_ii)   (correctly rounded)
+ *   y_i = RNE(RNE(v_i - sum_{k<i} R_ki y_k) / R_ii),
+ *   w_i = RNE(RNE(y_i - sum_{k>i} R_ik w_k) / R_ii),
+ *   lambda_t = RNE(RNE(<v,v>) / RNE(<v,w>)),  v <- w 2^-E (max |v_i| in [1/2,1)),
+ *   starting from v = (1, ..., 1).
+ * Every sum is exact; RNE is round to nearest, ties to even mantissa.
+ *
+ * Threading and streams: an hk_ctx is used by one host thread at a time.  All
+ * device work is issued on the context's stream; calls that return host data
+ * synchronise that stream before returning.
+ *
+ * Errors: every int-returning call returns an hk_status.  No call aborts the
+ * process; on error the context stays usable (a new hk_load_moments resets it).
+ */
+#ifndef HK_H
+#define HK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HK_OK = 0,
+  HK_ERR_ARG = 1,      /* bad argument (size, precision, null pointer, unnormalised value) */
+  HK_ERR_NOT_PD = 2,   /* a rounded pivot S_ii <= 0: P too small or M not positive definite */
+  HK_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+  HK_ERR_OOM = 4,      /* device allocation failed or caller workspace too small */
+  HK_ERR_TIMEOUT = 5,  /* a bounded device wait ran out (no hang; the kernel returned) */
+  HK_ERR_STATE = 6,    /* call out of order (e.g. hk_factor before hk_load_moments) */
+  HK_ERR_RANGE = 7     /* exact-accumulation window exhausted after all widenings */
+} hk_status;
+
+/* One P-bit number; the caller owns limbs[L]. */
+typedef struct {
+  int32_t sign;      /* 0 or 1 */
+  int64_t exp;       /* value = (-1)^sign * m * 2^exp */
+  uint32_t *limbs;   /* L little-endian 32-bit limbs of m */
+} hk_mp;
+
+typedef struct hk_ctx hk_ctx;
+
+/* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
+ * (NULL = the legacy default stream).  *ctx receives the handle. */
+int hk_create(hk_ctx **ctx, int device, void *cuda_stream);
+
+/* Release every device buffer the library allocated and the context. */
+void hk_destroy(hk_ctx *ctx);
+
+/* Human-readable text for a status code (static storage). */
+const char *hk_strerror(int code);
+
+/* Device bytes hk_factor + hk_smallest_eig need for order N at precision P
+ * (one widening of the exact-accumulation window included). */
+int hk_workspace_bytes(int N, int P, size_t *bytes);
+
+/* Use caller-owned device memory [dev_ptr, dev_ptr + bytes) as workspace
+ * instead of library allocations.  The caller keeps it alive until the
+ * context is destroyed or another workspace is set.  Too small -> HK_ERR_OOM
+ * at the first call that needs more. */
+int hk_set_workspace(hk_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* Load the 2N-1 moments m_0..m_{2N-2} (host array of hk_mp, copied to the
+ * device), defining M_ij = m_{i+j} (Introduction).  beta = beta_num/beta_den
+ * is recorded for reporting only; the moments define the matrix.  Requires
+ * 1 <= N, P a positive multiple of 32, every value normalised.  Resets any
+ * previous factorisation. */
+int hk_load_moments(hk_ctx *ctx, int N, int beta_num, int beta_den, int P,
+                    const hk_mp *moments);
+
+/* Same, from flat arrays: sign[2N-1] (int32), exp[2N-1] (int64) and
+ * limbs[(2N-1) * L] (uint32, moment k at limbs + k*L).  With on_device = 0
+ * the pointers are host memory (copied in); with on_device = 1 they are
+ * device memory already resident in HBM (copied device to device). */
+int hk_load_moments_flat(hk_ctx *ctx, int N, int beta_num, int beta_den, int P,
+                         const int32_t *sign, const int64_t *exp, const uint32_t *limbs,
+                         int on_device);
+
+/* Factor M = R^T R.  On HK_ERR_NOT_PD, *bad_row (if non-NULL) receives the
+ * first row whose rounded pivot is <= 0, as the oracle reports it. */
+int hk_factor(hk_ctx *ctx, int *bad_row);
+
+/* Copy R (row-major packed upper triangle, N(N+1)/2 entries, entry (t, j),
+ * j >= t, at index t*N - t*(t-1)/2 + (j - t)) to host hk_mp values whose
+ * limbs arrays the caller provides. */
+int hk_get_R(hk_ctx *ctx, hk_mp *R);
+
+/* Same into flat host arrays of N(N+1)/2 entries. */
+int hk_get_R_flat(hk_ctx *ctx, int32_t *sign, int64_t *exp, uint32_t *limbs);
+
+/* Inverse iteration after hk_factor.  iters > 0: exactly that many steps.
+ * iters == 0: until |lambda_t - lambda_{t-1}| <= 2^-136 lambda_t or 200 steps.
+ * *lambda_min receives lambda_T (caller-provided limbs[L]); *iters_used the
+ * step count. */
+int hk_smallest_eig(hk_ctx *ctx, int iters, hk_mp *lambda_min, int *iters_used);
+
+/* Last hk_smallest_eig history lambda_1..lambda_T into flat host arrays of
+ * `count` entries (count <= iters_used). */
+int hk_get_history_flat(hk_ctx *ctx, int count, int32_t *sign, int64_t *exp, uint32_t *limbs);
+
+/* Per-phase device times in milliseconds of the last hk_factor /
+ * hk_smallest_eig: out[0] update kernels, out[1] panel (diagonal and row)
+ * kernels, out[2] solve kernels, out[3] total factor, out[4] total
+ * inverse iteration.  n = number of doubles provided (<= 8). */
+int hk_get_timings(hk_ctx *ctx, double *out, int n);
+
+/* Launch statistics of the last hk_factor + hk_smallest_eig: out[0] kernels
+ * launched, out[1] exact-accumulation window width W in limbs, out[2]
+ * widenings taken. */
+int hk_get_stats(hk_ctx *ctx, int64_t *out, int n);
+
+/* ----- self-test hooks of the device multiprecision library ----------------
+ * Run one single-CTA device operation on host operands (copied in and out) so
+ * that tests can compare it with exact integer arithmetic:
+ *   op 0: out = x * y                       (nx, ny limbs; out nx+ny limbs)
+ *   op 1: out = floor(2^(2P+1) / x)          (x: L limbs normalised; out L+2)
+ *   op 2: out = RNE_P(sqrt(x * 2^e)) mantissa, *eo exponent (x: L limbs)
+ *   op 3: out = RNE_P((x 2^e) / (y 2^f)) mantissa, *eo exponent
+ *   op 4: out = RNE_P(|x| 2^e) of an nx-limb integer, *eo exponent
+ * `out` has room for the stated limbs. */
+int hk_selftest_mp(int op, int L, const uint32_t *x, int nx, int64_t ex,
+                   const uint32_t *y, int ny, int64_t ey, uint32_t *out, int64_t *eo);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HK_H */

@@ -1,0 +1,958 @@
+// libhk C ABI: context, device memory, and the order of kernel launches of the
+// factorisation and of inverse iteration.  All arithmetic of the method runs
+// in the kernels (hk_update.cu, hk_panel.cu, hk_solve.cu); this file only
+// sequences launches, sizes exact-accumulation windows and moves data.
+#include "hk.h"
+#include "hk_internal.h"
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <map>
+#include <new>
+#include <utility>
+#include <vector>
+
+using namespace hk;
+
+// largest precision whose panel work areas fit in one block's shared memory
+static const int HK_MAX_P = 32768;
+
+namespace {
+
+struct Arena {
+  char *base = nullptr;  // caller workspace (bump allocation) or null
+  size_t cap = 0, used = 0;
+  std::vector<void *> owned;
+  cudaError_t get(void **p, size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    if (base) {
+      if (used + bytes > cap) return cudaErrorMemoryAllocation;
+      *p = base + used;
+      used += bytes;
+      return cudaSuccess;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) owned.push_back(*p);
+    return e;
+  }
+  void release() {
+    for (void *p : owned) cudaFree(p);
+    owned.clear();
+  }
+};
+
+struct EvPair {
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct hk_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Arena base_arena, fac_arena, sol_arena;
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  // problem
+  int N = 0, L = 0, P = 0, bnum = 1, bden = 1;
+  bool loaded = false, factored = false;
+  int W = 0, C = 0, nb = 16, nbs = 16;
+  MpArr mom{};
+  long long *colU = nullptr, *colG = nullptr;
+  DevStatus *st = nullptr;
+  long long *d_range = nullptr;
+  // factor buffers
+  MpArr R{};
+  uint32_t *A = nullptr;
+  int32_t *Asign = nullptr;
+  uint32_t *recip = nullptr;
+  long long *colsum = nullptr;
+  std::map<std::pair<int, int>, std::pair<Unit *, int>> unit_cache;
+  // solve buffers
+  MpArr v{}, y{}, w{}, hist{};
+  int hist_cap = 0, hist_count = 0;
+  uint32_t *vecA = nullptr, *vecB = nullptr;
+  int32_t *vecAsign = nullptr, *vecBsign = nullptr;
+  size_t vec_cap = 0;  // limbs per vector buffer
+  long long *colsum_s = nullptr;
+  size_t colsum_s_cap = 0;  // int64 entries
+  bool sol_ready = false;
+  // timing / stats
+  std::vector<EvPair> evpool;
+  size_t evused = 0;
+  std::vector<int> evkind;  // 0 update, 1 panel, 2 solve
+  double t_phase[3] = {0, 0, 0};
+  double t_factor = 0, t_eig = 0;
+  long long launches = 0;
+  int widenings = 0;
+  long long top_margin = 0;  // extra bits above the a priori column bounds
+  bool timing = true;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return HK_OK;
+  if (e == cudaErrorMemoryAllocation) return HK_ERR_OOM;
+  return HK_ERR_CUDA;
+}
+
+#define CK(x)                                  \
+  do {                                         \
+    cudaError_t e_ = (x);                      \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+cudaError_t arena_get(hk_ctx *c, Arena &a, void **p, size_t bytes) {
+  if (c->ws) {
+    // all arenas share the caller workspace through the base arena
+    return c->base_arena.get(p, bytes);
+  }
+  return a.get(p, bytes);
+}
+
+template <typename T>
+cudaError_t alloc(hk_ctx *c, Arena &a, T **p, size_t count) {
+  void *q = nullptr;
+  cudaError_t e = arena_get(c, a, &q, count * sizeof(T));
+  *p = reinterpret_cast<T *>(q);
+  return e;
+}
+
+cudaError_t alloc_mp(hk_ctx *c, Arena &a, MpArr *m, size_t count, int L) {
+  cudaError_t e = alloc(c, a, &m->sign, count);
+  if (e == cudaSuccess) e = alloc(c, a, &m->exp, count);
+  if (e == cudaSuccess) e = alloc(c, a, &m->limbs, count * (size_t)L);
+  return e;
+}
+
+int round4(long long x) { return (int)((x + 3) / 4 * 4); }
+
+// --- event timing ---------------------------------------------------------------
+void ev_begin(hk_ctx *c, int kind) {
+  if (!c->timing) return;
+  if (c->evused == c->evpool.size()) {
+    EvPair p;
+    cudaEventCreate(&p.a);
+    cudaEventCreate(&p.b);
+    c->evpool.push_back(p);
+  }
+  if (c->evkind.size() < c->evpool.size()) c->evkind.resize(c->evpool.size());
+  c->evkind[c->evused] = kind;
+  cudaEventRecord(c->evpool[c->evused].a, c->stream);
+}
+void ev_end(hk_ctx *c) {
+  if (!c->timing) return;
+  cudaEventRecord(c->evpool[c->evused].b, c->stream);
+  c->evused++;
+}
+void ev_collect(hk_ctx *c) {
+  for (size_t k = 0; k < c->evused; k++) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, c->evpool[k].a, c->evpool[k].b);
+    c->t_phase[c->evkind[k]] += ms;
+  }
+  c->evused = 0;
+}
+
+cudaError_t units_for(hk_ctx *c, int Wx, int Wy, Unit **u, int *n) {
+  auto key = std::make_pair(Wx, Wy);
+  auto it = c->unit_cache.find(key);
+  if (it != c->unit_cache.end()) {
+    *u = it->second.first;
+    *n = it->second.second;
+    return cudaSuccess;
+  }
+  const int cnt = build_units(Wx, Wy, nullptr, 0);
+  std::vector<Unit> h(cnt);
+  build_units(Wx, Wy, h.data(), cnt);
+  Unit *d = nullptr;
+  cudaError_t e = alloc(c, c->base_arena, &d, (size_t)cnt);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(d, h.data(), sizeof(Unit) * cnt, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  c->unit_cache[key] = std::make_pair(d, cnt);
+  *u = d;
+  *n = cnt;
+  return cudaSuccess;
+}
+
+int sm_count(hk_ctx *c) {
+  int n = 0;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c->device);
+  return n > 0 ? n : 1;
+}
+
+// t per CTA so that a launch has roughly `target` blocks
+int pick_tchunk(int trange, long long blocks_per_chunk, long long target) {
+  if (trange <= 0) return 1;
+  long long nchunks = (target + blocks_per_chunk - 1) / std::max(1LL, blocks_per_chunk);
+  nchunks = std::max(1LL, std::min<long long>(nchunks, trange));
+  return (int)((trange + nchunks - 1) / nchunks);
+}
+
+long long rows_outputs(int N, int a, int b) {
+  long long s = 0;
+  for (int i = a; i < b; i++) s += N - i;
+  return s;
+}
+
+DevStatus read_status(hk_ctx *c) {
+  DevStatus s;
+  cudaMemcpyAsync(&s, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream);
+  cudaStreamSynchronize(c->stream);
+  return s;
+}
+
+cudaError_t reset_status(hk_ctx *c) {
+  DevStatus s;
+  std::memset(&s, 0, sizeof(s));
+  s.bad_row = INT_MAX;
+  return cudaMemcpyAsync(c->st, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream);
+}
+
+__global__ void k_col_grid(int N, const long long *colU, int W, long long *colG) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < N) colG[j] = colU[j] - 32LL * W;
+}
+
+// one attempt of the blocked factorisation with window width c->W
+int factor_attempt(hk_ctx *c) {
+  const int N = c->N, L = c->L, W = c->W, nb = c->nb;
+  c->fac_arena.release();
+  c->unit_cache.clear();
+  const size_t NT = (size_t)N * (N + 1) / 2;
+  CK(alloc_mp(c, c->fac_arena, &c->R, NT, L));
+  CK(alloc(c, c->fac_arena, &c->A, NT * (size_t)W));
+  CK(alloc(c, c->fac_arena, &c->Asign, NT));
+  CK(alloc(c, c->fac_arena, &c->recip, (size_t)N * (L + 2)));
+  c->C = colsum_width(W, W);
+  const long long maxout = rows_outputs(N, 0, std::min(nb, N));
+  CK(alloc(c, c->fac_arena, &c->colsum, (size_t)maxout * c->C));
+  Unit *units = nullptr;
+  int nunits = 0;
+  CK(units_for(c, W, W, &units, &nunits));
+  CK(reset_status(c));
+  CK(launch_col_tops(N, L, c->top_margin, c->mom, c->colU, c->st, c->stream));
+  k_col_grid<<<(N + 127) / 128, 128, 0, c->stream>>>(N, c->colU, W, c->colG);
+  CK(cudaGetLastError());
+  c->launches += 2;
+
+  PanelParams pp;
+  pp.N = N;
+  pp.L = L;
+  pp.W = W;
+  pp.C = c->C;
+  pp.mom = c->mom;
+  pp.colU = c->colU;
+  pp.R = c->R;
+  pp.A = c->A;
+  pp.Asign = c->Asign;
+  pp.recip = c->recip;
+  pp.colsum = c->colsum;
+  pp.st = c->st;
+
+  UpdParams up;
+  std::memset(&up, 0, sizeof(up));
+  up.mode = M_FACTOR;
+  up.N = N;
+  up.A = c->A;
+  up.Asign = c->Asign;
+  up.W = W;
+  up.Wx = W;
+  up.Wy = W;
+  up.colsum = c->colsum;
+  up.C = c->C;
+  up.units = units;
+  up.nunits = nunits;
+  up.st = c->st;
+  const long long cta_per_out = (nunits + UNT - 1) / UNT;
+  const long long target = 6LL * sm_count(c) * 3;
+
+  for (int r0 = 0; r0 < N; r0 += nb) {
+    const int r1 = std::min(N, r0 + nb);
+    const long long nout = rows_outputs(N, r0, r1);
+    CK(cudaMemsetAsync(c->colsum, 0, sizeof(long long) * nout * c->C, c->stream));
+    pp.r0 = r0;
+    up.r0 = r0;
+    if (r0 > 0) {
+      up.ra = r0;
+      up.rb = r1;
+      up.nout = (int)nout;
+      up.t0 = 0;
+      up.t1 = r0;
+      up.tchunk = pick_tchunk(r0, cta_per_out * nout, target);
+      ev_begin(c, 0);
+      CK(launch_update(up, c->stream));
+      ev_end(c);
+      c->launches++;
+    }
+    for (int i = r0; i < r1; i++) {
+      ev_begin(c, 1);
+      CK(launch_diag(pp, i, c->stream));
+      CK(launch_offdiag(pp, i, c->stream));
+      ev_end(c);
+      c->launches += (i + 1 < N) ? 2 : 1;
+      if (i + 1 < r1) {
+        up.ra = i + 1;
+        up.rb = r1;
+        up.nout = (int)rows_outputs(N, i + 1, r1);
+        up.t0 = i;
+        up.t1 = i + 1;
+        up.tchunk = 1;
+        ev_begin(c, 0);
+        CK(launch_update(up, c->stream));
+        ev_end(c);
+        c->launches++;
+      }
+    }
+  }
+  return HK_OK;
+}
+
+int ensure_solve_buffers(hk_ctx *c, int hist_need) {
+  const int N = c->N, L = c->L;
+  if (!c->sol_ready) {
+    CK(alloc_mp(c, c->sol_arena, &c->v, N, L));
+    CK(alloc_mp(c, c->sol_arena, &c->y, N, L));
+    CK(alloc_mp(c, c->sol_arena, &c->w, N, L));
+    c->sol_ready = true;
+  }
+  if (hist_need > c->hist_cap) {
+    const int cap = std::max(hist_need, 64);
+    CK(alloc_mp(c, c->sol_arena, &c->hist, cap, L));
+    c->hist_cap = cap;
+  }
+  return HK_OK;
+}
+
+int ensure_vec(hk_ctx *c, int Wv, int Cs, int rows) {
+  const size_t need = (size_t)c->N * Wv;
+  if (need > c->vec_cap) {
+    const size_t cap = need + need / 4 + 1024;
+    CK(alloc(c, c->sol_arena, &c->vecA, cap));
+    CK(alloc(c, c->sol_arena, &c->vecB, cap));
+    CK(alloc(c, c->sol_arena, &c->vecAsign, (size_t)c->N));
+    CK(alloc(c, c->sol_arena, &c->vecBsign, (size_t)c->N));
+    c->vec_cap = cap;
+  }
+  const size_t cneed = (size_t)rows * Cs;
+  if (cneed > c->colsum_s_cap) {
+    const size_t cap = cneed + cneed / 4 + 1024;
+    CK(alloc(c, c->sol_arena, &c->colsum_s, cap));
+    c->colsum_s_cap = cap;
+  }
+  return HK_OK;
+}
+
+int exprange(hk_ctx *c, int n, MpArr v, bool scaled, long long *lo, long long *hi) {
+  CK(launch_vec_exprange(n, v, c->L, c->colG, scaled ? 1 : 0, c->d_range, c->stream));
+  c->launches++;
+  long long h[2];
+  CK(cudaMemcpyAsync(h, c->d_range, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *lo = h[0];
+  *hi = h[1];
+  return HK_OK;
+}
+
+// one triangular solve: forward (R^T out = rhs) or back (R out = rhs)
+int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
+  const int N = c->N, L = c->L, W = c->W, nbs = c->nbs;
+  const long long P = 32LL * L;
+  std::vector<std::pair<int, int>> blocks;  // [B0, B1) in processing order
+  if (!back) {
+    blocks.push_back({0, 1});
+    for (int b = 1; b < N; b += nbs) blocks.push_back({b, std::min(N, b + nbs)});
+  } else {
+    blocks.push_back({N - 1, N});
+    for (int b = N - 1; b > 0; b -= nbs) blocks.push_back({std::max(0, b - nbs), b});
+  }
+  SolveParams sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.N = N;
+  sp.L = L;
+  sp.W = W;
+  sp.R = c->R;
+  sp.recip = c->recip;
+  sp.colU = c->colU;
+  sp.rhs = rhs;
+  sp.out = out;
+  sp.back = back ? 1 : 0;
+  sp.st = c->st;
+  long long margin = 256;
+  for (size_t bi = 0; bi < blocks.size(); bi++) {
+    const int B0 = blocks[bi].first, B1 = blocks[bi].second;
+    const int k0 = back ? B1 : 0, k1 = back ? N : B0;  // known entries
+    for (int attempt = 0;; attempt++) {
+      if (attempt > 6) return HK_ERR_RANGE;
+      long long h, top;
+      const bool have_known = k1 > k0;
+      if (have_known) {
+        // exact exponent range of the known entries (scaled by 2^g_k in the back solve)
+        MpArr sub = out;
+        sub.sign += k0;
+        sub.exp += k0;
+        sub.limbs += (size_t)k0 * L;
+        CK(launch_vec_exprange(k1 - k0, sub, L, c->colG + k0, back ? 1 : 0, c->d_range, c->stream));
+        c->launches++;
+        long long hh[2];
+        CK(cudaMemcpyAsync(hh, c->d_range, sizeof(hh), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        long long lo = hh[0], hi = hh[1];
+        if (lo == LLONG_MAX) {  // all known entries are zero
+          lo = 0;
+          hi = P;
+        }
+        h = lo - margin;
+        top = hi + margin;
+      } else {
+        h = 0;
+        top = 4 * 32;
+      }
+      sp.nosum = have_known ? 0 : 1;
+      const int Wv = std::max(4, round4((top - h + 31) / 32));
+      const int Cs = colsum_width(W, Wv);
+      int rc = ensure_vec(c, Wv, Cs, nbs);
+      if (rc) return rc;
+      sp.vecA = c->vecA;
+      sp.vecAsign = c->vecAsign;
+      sp.Wv = Wv;
+      sp.C = Cs;
+      sp.h = h;
+      sp.colsum = c->colsum_s;
+      sp.r0 = B0;
+      CK(cudaMemsetAsync(c->colsum_s, 0, sizeof(long long) * (size_t)(B1 - B0) * Cs, c->stream));
+      ev_begin(c, 2);
+      if (have_known) {
+        CK(launch_vec_align(k0, k1, out, L, c->colG, back ? 1 : 0, h, Wv, c->vecA, c->vecAsign, c->st,
+                            c->stream));
+        c->launches++;
+      }
+      Unit *units = nullptr;
+      int nunits = 0;
+      CK(units_for(c, W, Wv, &units, &nunits));
+      UpdParams up;
+      std::memset(&up, 0, sizeof(up));
+      up.mode = back ? M_GEMV_BACK : M_GEMV_FWD;
+      up.N = N;
+      up.A = c->A;
+      up.Asign = c->Asign;
+      up.W = W;
+      up.Vy = c->vecA;
+      up.Vysign = c->vecAsign;
+      up.Wv = Wv;
+      up.Wx = W;
+      up.Wy = Wv;
+      up.r0 = B0;
+      up.colsum = c->colsum_s;
+      up.C = Cs;
+      up.units = units;
+      up.nunits = nunits;
+      up.st = c->st;
+      const long long cta_per_out = (nunits + UNT - 1) / UNT;
+      const long long target = 6LL * sm_count(c) * 3;
+      if (have_known) {
+        up.ra = B0;
+        up.rb = B1;
+        up.nout = B1 - B0;
+        up.t0 = k0;
+        up.t1 = k1;
+        up.tchunk = pick_tchunk(k1 - k0, cta_per_out * (B1 - B0), target);
+        CK(launch_update(up, c->stream));
+        c->launches++;
+      }
+      sp.h = h;
+      for (int s = 0; s < B1 - B0; s++) {
+        const int i = back ? B1 - 1 - s : B0 + s;
+        // the first entry of each solve has no sum: the kernel takes G from the rhs
+        CK(launch_solve_entry(sp, i, c->stream));
+        c->launches++;
+        const bool more = back ? (i > B0) : (i + 1 < B1);
+        if (more) {
+          if (back) {
+            up.ra = B0;
+            up.rb = i;
+          } else {
+            up.ra = i + 1;
+            up.rb = B1;
+          }
+          up.nout = up.rb - up.ra;
+          up.t0 = i;
+          up.t1 = i + 1;
+          up.tchunk = 1;
+          CK(launch_update(up, c->stream));
+          c->launches++;
+        }
+      }
+      ev_end(c);
+      DevStatus st = read_status(c);
+      if (st.code != ST_OK) return st.code == ST_NOT_PD ? HK_ERR_NOT_PD : HK_ERR_CUDA;
+      if (st.timeout) return HK_ERR_TIMEOUT;
+      if (st.range_fail) {
+        margin = margin * 4 + st.need_bits;
+        CK(reset_status(c));
+        continue;
+      }
+      break;
+    }
+  }
+  return HK_OK;
+}
+
+// lambda_t from <v,v> and <v,w>
+int rayleigh(hk_ctx *c, int slot) {
+  const int N = c->N, L = c->L;
+  long long lov, hiv, low, hiw;
+  int rc = exprange(c, N, c->v, false, &lov, &hiv);
+  if (rc) return rc;
+  rc = exprange(c, N, c->w, false, &low, &hiw);
+  if (rc) return rc;
+  if (lov == LLONG_MAX || low == LLONG_MAX) return HK_ERR_NOT_PD;
+  const int Wd = std::max(4, round4(std::max((hiv - lov + 31) / 32, (hiw - low + 31) / 32)));
+  const int Cd = colsum_width(Wd, Wd);
+  rc = ensure_vec(c, Wd, Cd, 2);
+  if (rc) return rc;
+  ev_begin(c, 2);
+  CK(launch_vec_align(0, N, c->v, L, nullptr, 0, lov, Wd, c->vecA, c->vecAsign, c->st, c->stream));
+  CK(launch_vec_align(0, N, c->w, L, nullptr, 0, low, Wd, c->vecB, c->vecBsign, c->st, c->stream));
+  CK(cudaMemsetAsync(c->colsum_s, 0, sizeof(long long) * 2 * Cd, c->stream));
+  Unit *units = nullptr;
+  int nunits = 0;
+  CK(units_for(c, Wd, Wd, &units, &nunits));
+  UpdParams up;
+  std::memset(&up, 0, sizeof(up));
+  up.mode = M_DOT;
+  up.N = N;
+  up.Vx = c->vecA;
+  up.Vxsign = c->vecAsign;
+  up.Vy = c->vecB;
+  up.Vysign = c->vecBsign;
+  up.Wv = Wd;
+  up.Wx = Wd;
+  up.Wy = Wd;
+  up.nout = 2;
+  up.t0 = 0;
+  up.t1 = N;
+  up.colsum = c->colsum_s;
+  up.C = Cd;
+  up.units = units;
+  up.nunits = nunits;
+  up.st = c->st;
+  const long long cta_per_out = (nunits + UNT - 1) / UNT;
+  up.tchunk = pick_tchunk(N, cta_per_out * 2, 6LL * sm_count(c) * 3);
+  CK(launch_update(up, c->stream));
+  CK(launch_lambda(L, c->colsum_s, Cd, lov, low, c->hist, slot, c->st, c->stream));
+  ev_end(c);
+  c->launches += 4;
+  return HK_OK;
+}
+
+// |a - b| <= 2^-136 a for positive normalised P-bit values (stopping rule
+// of the run-until-converged mode; exact host comparison of two mantissas)
+bool converged(long long ea, const uint32_t *la, long long eb, const uint32_t *lb, int L) {
+  if (ea - eb > 1 || eb - ea > 1) return false;
+  std::vector<uint32_t> A(L + 1, 0), B(L + 1, 0);
+  for (int l = 0; l < L; l++) {
+    A[l] = la[l];
+    B[l] = lb[l];
+  }
+  long long e = std::min(ea, eb);
+  auto dbl = [&](std::vector<uint32_t> &X) {
+    uint32_t carry = 0;
+    for (int l = 0; l <= L; l++) {
+      const uint32_t nc = X[l] >> 31;
+      X[l] = (X[l] << 1) | carry;
+      carry = nc;
+    }
+  };
+  if (ea > eb) dbl(A);
+  if (eb > ea) dbl(B);
+  bool ge = true;
+  for (int l = L; l >= 0; l--)
+    if (A[l] != B[l]) {
+      ge = A[l] > B[l];
+      break;
+    }
+  std::vector<uint32_t> D(L + 1, 0);
+  const std::vector<uint32_t> &X = ge ? A : B, &Y = ge ? B : A;
+  long long borrow = 0;
+  for (int l = 0; l <= L; l++) {
+    long long v = (long long)X[l] - (long long)Y[l] - borrow;
+    borrow = v < 0;
+    D[l] = (uint32_t)(v + (borrow ? (1LL << 32) : 0));
+  }
+  long long bl = 0;
+  for (int l = L; l >= 0; l--)
+    if (D[l]) {
+      bl = 32LL * l + 32 - __builtin_clz(D[l]);
+      break;
+    }
+  if (bl == 0) return true;
+  const long long P = 32LL * L;
+  return bl + e <= P + ea - 137;
+}
+
+}  // namespace
+
+// ============================== C ABI =========================================
+
+extern "C" {
+
+const char *hk_strerror(int code) {
+  switch (code) {
+    case HK_OK: return "ok";
+    case HK_ERR_ARG: return "invalid argument";
+    case HK_ERR_NOT_PD: return "rounded pivot <= 0 (matrix not positive definite at this precision)";
+    case HK_ERR_CUDA: return "CUDA runtime error";
+    case HK_ERR_OOM: return "out of device memory";
+    case HK_ERR_TIMEOUT: return "bounded device wait ran out";
+    case HK_ERR_STATE: return "call out of order";
+    case HK_ERR_RANGE: return "exact-accumulation window exhausted";
+    default: return "unknown status";
+  }
+}
+
+int hk_create(hk_ctx **out, int device, void *cuda_stream) {
+  if (!out) return HK_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return HK_ERR_ARG;
+  hk_ctx *c = new (std::nothrow) hk_ctx();
+  if (!c) return HK_ERR_OOM;
+  c->device = device;
+  c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete c;
+    return HK_ERR_CUDA;
+  }
+  *out = c;
+  return HK_OK;
+}
+
+void hk_destroy(hk_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  c->sol_arena.release();
+  c->fac_arena.release();
+  c->base_arena.release();
+  for (auto &p : c->evpool) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  delete c;
+}
+
+int hk_workspace_bytes(int N, int P, size_t *bytes) {
+  if (N < 1 || P < 32 || P % 32 || !bytes) return HK_ERR_ARG;
+  const long long L = P / 32;
+  const long long W = round4(L + (N + 128 + 31) / 32) + 64;  // one widening included
+  const long long NT = (long long)N * (N + 1) / 2;
+  const long long C = colsum_width((int)W, (int)W);
+  long long b = 0;
+  b += (2LL * N) * (16 + 4 * L);          // moments
+  b += 3LL * N * 8 + 4096;                // tops, grids, status
+  b += NT * (16 + 4 * L);                 // R
+  b += NT * (4 * W + 4);                  // aligned R
+  b += (long long)N * (L + 2) * 4;        // reciprocals
+  b += 16LL * N * C * 8;                  // column sums of one block
+  b += 3LL * N * (16 + 4 * L) + 256LL * (16 + 4 * L);  // v, y, w, history
+  const long long Wv = 2 * W + (long long)N;  // vector window (generous)
+  b += 2LL * N * (4 * Wv + 4) * 5 / 4 + 16LL * colsum_width((int)W, (int)Wv) * 8 * 5 / 4;
+  b += 1LL << 20;                         // unit tables, alignment slack
+  *bytes = (size_t)b * 2;                 // two widenings of slack for the bump allocator
+  return HK_OK;
+}
+
+int hk_set_workspace(hk_ctx *c, void *dev_ptr, size_t bytes) {
+  if (!c || (!dev_ptr && bytes)) return HK_ERR_ARG;
+  cudaSetDevice(c->device);
+  c->sol_arena.release();
+  c->fac_arena.release();
+  c->base_arena.release();
+  c->ws = reinterpret_cast<char *>(dev_ptr);
+  c->ws_bytes = bytes;
+  c->base_arena.base = c->ws;
+  c->base_arena.cap = bytes;
+  c->base_arena.used = 0;
+  c->loaded = c->factored = c->sol_ready = false;
+  c->hist_cap = 0;
+  c->vec_cap = 0;
+  c->colsum_s_cap = 0;
+  c->unit_cache.clear();
+  return HK_OK;
+}
+
+int hk_load_moments_flat(hk_ctx *c, int N, int bnum, int bden, int P, const int32_t *sign,
+                         const int64_t *exp, const uint32_t *limbs, int on_device) {
+  if (!c || N < 1 || P < 32 || P % 32 || P > HK_MAX_P || !sign || !exp || !limbs) return HK_ERR_ARG;
+  if ((long long)N * (N + 1) / 2 > (1LL << 40)) return HK_ERR_ARG;
+  cudaSetDevice(c->device);
+  const int L = P / 32;
+  const int M = 2 * N - 1;
+  if (!on_device) {
+    for (int k = 0; k < M; k++) {
+      const uint32_t *m = limbs + (size_t)k * L;
+      bool nz = false;
+      for (int l = 0; l < L; l++) nz |= m[l] != 0;
+      if (sign[k] != 0 && sign[k] != 1) return HK_ERR_ARG;
+      if (nz && !(m[L - 1] & 0x80000000u)) return HK_ERR_ARG;
+      if (!nz && (sign[k] != 0 || exp[k] != 0)) return HK_ERR_ARG;
+    }
+  }
+  cudaStreamSynchronize(c->stream);
+  c->sol_arena.release();
+  c->fac_arena.release();
+  c->base_arena.release();
+  if (c->ws) {
+    c->base_arena.base = c->ws;
+    c->base_arena.cap = c->ws_bytes;
+    c->base_arena.used = 0;
+  }
+  c->unit_cache.clear();
+  c->loaded = c->factored = c->sol_ready = false;
+  c->hist_cap = 0;
+  c->hist_count = 0;
+  c->vec_cap = 0;
+  c->colsum_s_cap = 0;
+  c->N = N;
+  c->L = L;
+  c->P = P;
+  c->bnum = bnum;
+  c->bden = bden;
+  CK(alloc_mp(c, c->base_arena, &c->mom, M, L));
+  CK(alloc(c, c->base_arena, &c->colU, (size_t)N));
+  CK(alloc(c, c->base_arena, &c->colG, (size_t)N));
+  CK(alloc(c, c->base_arena, &c->st, 1));
+  CK(alloc(c, c->base_arena, &c->d_range, 2));
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(c->mom.sign, sign, sizeof(int32_t) * M, kind, c->stream));
+  CK(cudaMemcpyAsync(c->mom.exp, exp, sizeof(long long) * M, kind, c->stream));
+  CK(cudaMemcpyAsync(c->mom.limbs, limbs, sizeof(uint32_t) * (size_t)M * L, kind, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->loaded = true;
+  return HK_OK;
+}
+
+int hk_load_moments(hk_ctx *c, int N, int bnum, int bden, int P, const hk_mp *moments) {
+  if (!c || N < 1 || P < 32 || P % 32 || !moments) return HK_ERR_ARG;
+  const int L = P / 32, M = 2 * N - 1;
+  std::vector<int32_t> s(M);
+  std::vector<int64_t> e(M);
+  std::vector<uint32_t> l((size_t)M * L);
+  for (int k = 0; k < M; k++) {
+    if (!moments[k].limbs) return HK_ERR_ARG;
+    s[k] = moments[k].sign;
+    e[k] = moments[k].exp;
+    std::memcpy(&l[(size_t)k * L], moments[k].limbs, sizeof(uint32_t) * L);
+  }
+  return hk_load_moments_flat(c, N, bnum, bden, P, s.data(), e.data(), l.data(), 0);
+}
+
+int hk_factor(hk_ctx *c, int *bad_row) {
+  if (!c) return HK_ERR_ARG;
+  if (!c->loaded) return HK_ERR_STATE;
+  cudaSetDevice(c->device);
+  c->factored = false;
+  c->sol_ready = false;
+  c->sol_arena.release();
+  c->hist_cap = 0;
+  c->vec_cap = 0;
+  c->colsum_s_cap = 0;
+  c->launches = 0;
+  c->widenings = 0;
+  c->t_phase[0] = c->t_phase[1] = c->t_phase[2] = 0;
+  c->W = round4(c->L + (c->N + 128 + 31) / 32);
+  c->top_margin = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int result = HK_ERR_RANGE;
+  for (int attempt = 0; attempt < 4; attempt++) {
+    c->evused = 0;
+    cudaEventRecord(e0, c->stream);
+    int rc = factor_attempt(c);
+    cudaEventRecord(e1, c->stream);
+    if (rc != HK_OK) {
+      result = rc;
+      break;
+    }
+    DevStatus st = read_status(c);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    c->t_factor = ms;
+    c->t_phase[0] = c->t_phase[1] = 0;
+    ev_collect(c);
+    if (st.timeout) {
+      result = HK_ERR_TIMEOUT;
+      break;
+    }
+    // a window failure invalidates everything after it (including a later
+    // pivot test): widen the window below and above, and start again
+    if (st.range_fail) {
+      const long long delta = (st.need_bits + 64 + 31) / 32 * 32;
+      c->top_margin += delta;
+      c->W = round4(c->W + 2 * delta / 32);
+      c->widenings++;
+      continue;
+    }
+    if (st.code == ST_NOT_PD) {
+      if (bad_row) *bad_row = st.bad_row;
+      result = HK_ERR_NOT_PD;
+      break;
+    }
+    c->factored = true;
+    result = HK_OK;
+    break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return result;
+}
+
+int hk_get_R_flat(hk_ctx *c, int32_t *sign, int64_t *exp, uint32_t *limbs) {
+  if (!c || !sign || !exp || !limbs) return HK_ERR_ARG;
+  if (!c->factored) return HK_ERR_STATE;
+  cudaSetDevice(c->device);
+  const size_t NT = (size_t)c->N * (c->N + 1) / 2;
+  CK(cudaMemcpyAsync(sign, c->R.sign, sizeof(int32_t) * NT, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(exp, c->R.exp, sizeof(int64_t) * NT, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(limbs, c->R.limbs, sizeof(uint32_t) * NT * c->L, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return HK_OK;
+}
+
+int hk_get_R(hk_ctx *c, hk_mp *R) {
+  if (!c || !R) return HK_ERR_ARG;
+  if (!c->factored) return HK_ERR_STATE;
+  const size_t NT = (size_t)c->N * (c->N + 1) / 2;
+  std::vector<int32_t> s(NT);
+  std::vector<int64_t> e(NT);
+  std::vector<uint32_t> l(NT * c->L);
+  int rc = hk_get_R_flat(c, s.data(), e.data(), l.data());
+  if (rc) return rc;
+  for (size_t k = 0; k < NT; k++) {
+    if (!R[k].limbs) return HK_ERR_ARG;
+    R[k].sign = s[k];
+    R[k].exp = e[k];
+    std::memcpy(R[k].limbs, &l[k * c->L], sizeof(uint32_t) * c->L);
+  }
+  return HK_OK;
+}
+
+int hk_smallest_eig(hk_ctx *c, int iters, hk_mp *lambda_min, int *iters_used) {
+  if (!c || iters < 0) return HK_ERR_ARG;
+  if (!c->factored) return HK_ERR_STATE;
+  cudaSetDevice(c->device);
+  const int T = iters > 0 ? iters : 200;
+  int rc = ensure_solve_buffers(c, T);
+  if (rc) return rc;
+  c->t_phase[2] = 0;
+  c->evused = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, c->stream);
+  CK(launch_set_ones(c->N, c->v, c->L, c->stream));
+  c->launches++;
+  CK(reset_status(c));
+  const int L = c->L;
+  std::vector<uint32_t> prev(L), cur(L);
+  long long eprev = 0, ecur = 0;
+  int32_t sprev = 0, scur = 0;
+  int t = 0;
+  for (t = 0; t < T; t++) {
+    rc = solve(c, c->v, c->y, false);
+    if (rc) break;
+    rc = solve(c, c->y, c->w, true);
+    if (rc) break;
+    rc = rayleigh(c, t);
+    if (rc) break;
+    rc = cuda_status(launch_vec_normalise(c->N, c->w, c->v, L, c->stream));
+    c->launches++;
+    if (rc) break;
+    if (iters == 0) {
+      CK(cudaMemcpyAsync(cur.data(), c->hist.limbs + (size_t)t * L, 4 * (size_t)L, cudaMemcpyDeviceToHost,
+                         c->stream));
+      CK(cudaMemcpyAsync(&ecur, c->hist.exp + t, 8, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaMemcpyAsync(&scur, c->hist.sign + t, 4, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      if (t > 0 && converged(ecur, cur.data(), eprev, prev.data(), L)) {
+        t++;
+        break;
+      }
+      prev = cur;
+      eprev = ecur;
+      sprev = scur;
+    }
+  }
+  (void)sprev;
+  cudaEventRecord(e1, c->stream);
+  cudaEventSynchronize(e1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  c->t_eig = ms;
+  ev_collect(c);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  DevStatus st = read_status(c);
+  if (st.code == ST_NOT_PD) return HK_ERR_NOT_PD;
+  if (st.timeout) return HK_ERR_TIMEOUT;
+  const int used = std::min(t, T);
+  c->hist_count = used;
+  if (iters_used) *iters_used = used;
+  if (lambda_min && used > 0) {
+    if (!lambda_min->limbs) return HK_ERR_ARG;
+    const int k = used - 1;
+    CK(cudaMemcpyAsync(lambda_min->limbs, c->hist.limbs + (size_t)k * L, 4 * (size_t)L,
+                       cudaMemcpyDeviceToHost, c->stream));
+    long long e = 0;
+    int32_t s = 0;
+    CK(cudaMemcpyAsync(&e, c->hist.exp + k, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&s, c->hist.sign + k, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    lambda_min->exp = e;
+    lambda_min->sign = s;
+  }
+  return HK_OK;
+}
+
+int hk_get_history_flat(hk_ctx *c, int count, int32_t *sign, int64_t *exp, uint32_t *limbs) {
+  if (!c || count < 0 || !sign || !exp || !limbs) return HK_ERR_ARG;
+  if (count > c->hist_count) return HK_ERR_ARG;
+  if (count == 0) return HK_OK;
+  CK(cudaMemcpyAsync(sign, c->hist.sign, 4 * (size_t)count, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(exp, c->hist.exp, 8 * (size_t)count, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(limbs, c->hist.limbs, 4 * (size_t)count * c->L, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return HK_OK;
+}
+
+int hk_get_timings(hk_ctx *c, double *out, int n) {
+  if (!c || !out || n < 0) return HK_ERR_ARG;
+  const double v[5] = {c->t_phase[0], c->t_phase[1], c->t_phase[2], c->t_factor, c->t_eig};
+  for (int k = 0; k < n && k < 5; k++) out[k] = v[k];
+  for (int k = 5; k < n; k++) out[k] = 0;
+  return HK_OK;
+}
+
+int hk_get_stats(hk_ctx *c, int64_t *out, int n) {
+  if (!c || !out || n < 0) return HK_ERR_ARG;
+  const int64_t v[3] = {c->launches, c->W, c->widenings};
+  for (int k = 0; k < n && k < 3; k++) out[k] = v[k];
+  for (int k = 3; k < n; k++) out[k] = 0;
+  return HK_OK;
+}
+
+int hk_selftest_mp(int op, int L, const uint32_t *x, int nx, int64_t ex, const uint32_t *y, int ny,
+                   int64_t ey, uint32_t *out, int64_t *eo) {
+  if (!x || !out || !eo || (ny > 0 && !y)) return HK_ERR_ARG;
+  const int rc = hk::selftest_mp(op, L, x, nx, ex, y, ny, ey, out, eo);
+  return rc == 0 ? HK_OK : (rc == 1 ? HK_ERR_ARG : HK_ERR_CUDA);
+}
+
+}  // extern "C"

@@ -1,0 +1,271 @@
+// Panel kernels of the factorisation: for row i of R
+//   S_ij = RNE_P(m_{i+j} - sum_{t<i} R_ti R_tj)   (the sum arrives exactly as
+//          column sums from the update kernel, on the grid g_i + g_j)
+//   R_ii = RNE_P(sqrt(S_ii)),  R_ij = RNE_P(S_ij / R_ii)
+// (section "The LDL^T Determinant Algorithm": the diagonal entry, then the
+// column divided by it, CDivDiag[row] = M[row][pc] / M[pc][pc]; here with the
+// square root of the Cholesky form).  Each new entry is also written on the
+// binary grid of its column for the next updates ("alignment").
+#include "hk_internal.h"
+#include "hk_mp.cuh"
+
+namespace hk {
+
+namespace {
+
+constexpr int NT_DIAG = 256;
+constexpr int NT_ROW = 128;
+
+// a priori top bit bound of column j: |R_tj| <= sqrt(m_2j) < 2^U_j
+__global__ void k_col_tops(int N, int L, MpArr mom, long long *colU, long long top_margin) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const long long P = 32LL * L;
+  const int k = 2 * j;
+  long long e = mom.exp[k];
+  bool nz = false;
+  for (int l = 0; l < L; l++) nz |= mom.limbs[(long long)k * L + l] != 0;
+  if (!nz && k > 0) e = mom.exp[k - 1];  // degenerate moment: borrow a neighbour's scale
+  colU[j] = ((e + P + 1) >> 1) + 2 + top_margin;
+}
+
+struct RowSmem {
+  mp::Red *red;
+  long long *cs;
+  uint32_t *tmp, *Z, *mant, *big, *q, *V, *rm, *res;
+  uint32_t *nb[6];
+  uint32_t *xs;
+  int cap, cap4;
+};
+
+__host__ __device__ inline int row_cap(int L, int C) {
+  const int a = C + L + 24, b = 4 * L + 64;
+  return ((a > b ? a : b) + 3) / 4 * 4;
+}
+
+// Lays out the buffers from `base` (or only measures them when base is null);
+// returns the number of bytes used.
+__host__ __device__ inline size_t carve(unsigned char *base, int L, int C, bool diag, RowSmem *out) {
+  RowSmem s;
+  s.cap = row_cap(L, C);
+  s.cap4 = ((4 * L + 64) + 3) / 4 * 4;
+  size_t off = 0;
+  auto at = [&](size_t bytes) {
+    unsigned char *r = base ? base + off : nullptr;
+    off += (bytes + 15) / 16 * 16;
+    return r;
+  };
+  s.red = reinterpret_cast<mp::Red *>(at(sizeof(mp::Red)));
+  s.cs = reinterpret_cast<long long *>(at(8 * (size_t)s.cap));
+  auto take = [&](int n) { return reinterpret_cast<uint32_t *>(at(4 * (size_t)n)); };
+  s.tmp = take(s.cap);
+  s.Z = take(s.cap);
+  s.mant = take(L + 8);
+  s.big = take(s.cap4);
+  s.q = take(L + 8);
+  s.V = take(L + 8);
+  s.rm = take(L + 8);
+  s.res = take(L + 8);
+  if (diag) {
+    for (int k = 0; k < 6; k++) s.nb[k] = take(s.cap4);
+    s.xs = take(L + 8);
+  } else {
+    for (int k = 0; k < 6; k++) s.nb[k] = nullptr;
+    s.xs = nullptr;
+  }
+  if (out) *out = s;
+  return off;
+}
+
+__host__ __device__ inline size_t carve_size(int L, int C, bool diag) { return carve(nullptr, L, C, diag, nullptr); }
+
+HK_DEV mp::Work work_of(RowSmem &s) {
+  mp::Work w;
+  w.cs = s.cs;
+  w.tmp = s.tmp;
+  w.r = s.red;
+  return w;
+}
+
+// Z = (-1)^sm * m * 2^(em - G) - colsum  as magnitude in s.Z, returns
+// sign (+1 / -1) or 0 when the window is too narrow (range failure recorded).
+template <int NT>
+HK_DEV int form_exact(RowSmem &s, const long long *colrow, int C, int32_t sm, long long em,
+                      const uint32_t *ml, int L, long long G, DevStatus *st, int *nZ_out) {
+  const long long sh = em - G;
+  if (sh < 0) {
+    if (threadIdx.x == 0) raise_range(st, -sh);
+    return 0;
+  }
+  const long long q = sh >> 5;
+  const int b = (int)(sh & 31);
+  const int nm = (int)(q + L + 1);
+  const int nZ = max(C, nm);
+  if (nZ + 2 > s.cap) {
+    if (threadIdx.x == 0) raise_range(st, 32LL * (nZ + 2 - s.cap));
+    return 0;
+  }
+  for (int d = threadIdx.x; d < nZ; d += NT) {
+    const long long li = d - q;
+    const uint32_t a = mp::limb_at(ml, L, li), c = mp::limb_at(ml, L, li - 1);
+    const uint32_t mv = b ? ((a << b) | (c >> (32 - b))) : a;
+    const long long cv = d < C ? colrow[d] : 0;
+    s.cs[d] = (sm ? -(long long)mv : (long long)mv) - cv;
+  }
+  __syncthreads();
+  const bool neg = mp::resolve<NT>(s.cs, nZ, s.Z, *s.red);
+  *nZ_out = nZ + 2;
+  return neg ? -1 : 1;
+}
+
+// write value (sign, mant, exp) on column grid g as W limbs; false on range failure
+template <int NT>
+HK_DEV bool align_entry(const uint32_t *mant, int L, long long e, bool zero, long long g, int W,
+                        uint32_t *dst, DevStatus *st) {
+  if (zero) {
+    for (int l = threadIdx.x; l < W; l += NT) dst[l] = 0;
+    return true;
+  }
+  const long long sh = e - g;
+  const long long P = 32LL * L;
+  if (sh < 0 || sh + P > 32LL * W) {
+    if (threadIdx.x == 0) raise_range(st, sh < 0 ? -sh : sh + P - 32LL * W);
+    return false;
+  }
+  mp::shl<NT>(mant, L, sh, dst, W);
+  return true;
+}
+
+__global__ void __launch_bounds__(NT_DIAG) k_diag(PanelParams p, int i) {
+  if (p.st->code != ST_OK) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RowSmem s;
+  carve(smem_raw, p.L, p.C, true, &s);
+  mp::Work w = work_of(s);
+  const int L = p.L, N = p.N;
+  const long long P = 32LL * L;
+  const long long gi = p.colU[i] - 32LL * p.W;
+  const long long k = i - p.r0;
+  const long long crow = k * N - (k * (i + p.r0 - 1)) / 2;
+  const long long *colrow = p.colsum + crow * p.C;
+  const int mk = 2 * i;
+  int nZ = 0;
+  const int sgn = form_exact<NT_DIAG>(s, colrow, p.C, p.mom.sign[mk], p.mom.exp[mk],
+                                      p.mom.limbs + (long long)mk * L, L, 2 * gi, p.st, &nZ);
+  if (sgn == 0) return;
+  const mp::Rounded S = mp::round_rne<NT_DIAG>(s.Z, nZ, 2 * gi, L, s.mant, w);
+  if (!S.nonzero || sgn < 0) {
+    if (threadIdx.x == 0) {
+      atomicMin(&p.st->bad_row, i);
+      atomicCAS(&p.st->code, ST_OK, ST_NOT_PD);
+    }
+    return;
+  }
+  mp::NBufs B;
+  for (int t = 0; t < 6; t++) (&B.a)[t] = s.nb[t];
+  B.cap = s.cap4;
+  bool ok = true;
+  const mp::Rounded Rr = mp::sqrt_rne<NT_DIAG>(s.mant, L, S.exp, s.rm, w, B, s.big, s.xs, &ok);
+  const long long idx = tri_idx(i, i, N);
+  for (int l = threadIdx.x; l < L; l += NT_DIAG) p.R.limbs[idx * L + l] = s.rm[l];
+  if (threadIdx.x == 0) {
+    p.R.sign[idx] = 0;
+    p.R.exp[idx] = Rr.exp;
+    p.Asign[idx] = 0;
+    if (!ok) atomicAdd(&p.st->timeout, 1);
+  }
+  align_entry<NT_DIAG>(s.rm, L, Rr.exp, false, gi, p.W, p.A + idx * p.W, p.st);
+  __syncthreads();
+  ok = mp::recip<NT_DIAG>(s.rm, L, s.V, w, B);
+  for (int l = threadIdx.x; l < L + 2; l += NT_DIAG) p.recip[(long long)i * (L + 2) + l] = s.V[l];
+  if (threadIdx.x == 0 && !ok) atomicAdd(&p.st->timeout, 1);
+  (void)P;
+}
+
+__global__ void __launch_bounds__(NT_ROW) k_offdiag(PanelParams p, int i) {
+  if (p.st->code != ST_OK) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RowSmem s;
+  carve(smem_raw, p.L, p.C, false, &s);
+  mp::Work w = work_of(s);
+  const int L = p.L, N = p.N;
+  const int j = i + 1 + blockIdx.x;
+  const long long gi = p.colU[i] - 32LL * p.W;
+  const long long gj = p.colU[j] - 32LL * p.W;
+  const long long k = i - p.r0;
+  const long long crow = k * N - (k * (i + p.r0 - 1)) / 2 + (j - i);
+  const long long *colrow = p.colsum + crow * p.C;
+  const int mk = i + j;
+  int nZ = 0;
+  const int sgn = form_exact<NT_ROW>(s, colrow, p.C, p.mom.sign[mk], p.mom.exp[mk],
+                                     p.mom.limbs + (long long)mk * L, L, gi + gj, p.st, &nZ);
+  if (sgn == 0) return;
+  const mp::Rounded S = mp::round_rne<NT_ROW>(s.Z, nZ, gi + gj, L, s.mant, w);
+  const long long idx = tri_idx(i, j, N);
+  const long long iidx = tri_idx(i, i, N);
+  if (!S.nonzero) {
+    for (int l = threadIdx.x; l < L; l += NT_ROW) p.R.limbs[idx * L + l] = 0;
+    for (int l = threadIdx.x; l < p.W; l += NT_ROW) p.A[idx * p.W + l] = 0;
+    if (threadIdx.x == 0) {
+      p.R.sign[idx] = 0;
+      p.R.exp[idx] = 0;
+      p.Asign[idx] = 0;
+    }
+    return;
+  }
+  for (int l = threadIdx.x; l < L; l += NT_ROW) s.rm[l] = p.R.limbs[iidx * L + l];
+  for (int l = threadIdx.x; l < L + 2; l += NT_ROW) s.V[l] = p.recip[(long long)i * (L + 2) + l];
+  __syncthreads();
+  bool ok = true;
+  const mp::Rounded Q = mp::div_rne<NT_ROW>(s.mant, S.exp, s.rm, p.R.exp[iidx], s.V, L, s.res, w, s.big, s.q, &ok);
+  for (int l = threadIdx.x; l < L; l += NT_ROW) p.R.limbs[idx * L + l] = s.res[l];
+  if (threadIdx.x == 0) {
+    p.R.sign[idx] = sgn < 0 ? 1 : 0;
+    p.R.exp[idx] = Q.exp;
+    p.Asign[idx] = sgn < 0 ? 1 : 0;
+    if (!ok) atomicAdd(&p.st->timeout, 1);
+  }
+  align_entry<NT_ROW>(s.res, L, Q.exp, false, gj, p.W, p.A + idx * p.W, p.st);
+}
+
+}  // namespace
+
+size_t panel_smem_diag(int L, int C) { return carve_size(L, C, true); }
+size_t panel_smem_row(int L, int C) { return carve_size(L, C, false); }
+
+cudaError_t launch_col_tops(int N, int L, long long top_margin, MpArr mom, long long *colU, DevStatus *st,
+                            cudaStream_t s) {
+  (void)st;
+  k_col_tops<<<(N + 127) / 128, 128, 0, s>>>(N, L, mom, colU, top_margin);
+  return cudaGetLastError();
+}
+
+static cudaError_t set_smem(const void *fn, size_t bytes, size_t *done) {
+  if (bytes > 48 * 1024 && bytes > *done) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    *done = bytes;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_diag(const PanelParams &p, int i, cudaStream_t s) {
+  static size_t done = 0;
+  const size_t smem = panel_smem_diag(p.L, p.C);
+  cudaError_t e = set_smem((const void *)k_diag, smem, &done);
+  if (e != cudaSuccess) return e;
+  k_diag<<<1, NT_DIAG, smem, s>>>(p, i);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_offdiag(const PanelParams &p, int i, cudaStream_t s) {
+  if (i + 1 >= p.N) return cudaSuccess;
+  static size_t done = 0;
+  const size_t smem = panel_smem_row(p.L, p.C);
+  cudaError_t e = set_smem((const void *)k_offdiag, smem, &done);
+  if (e != cudaSuccess) return e;
+  k_offdiag<<<p.N - i - 1, NT_ROW, smem, s>>>(p, i);
+  return cudaGetLastError();
+}
+
+}  // namespace hk

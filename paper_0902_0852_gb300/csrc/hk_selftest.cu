@@ -1,0 +1,99 @@
+// Single-block driver of the device multiprecision library for unit tests:
+// operands and work areas live in global memory, one operation per launch.
+#include "hk_internal.h"
+#include "hk_mp.cuh"
+#include <vector>
+
+namespace hk {
+
+namespace {
+
+constexpr int NT_ST = 128;
+
+__global__ void __launch_bounds__(NT_ST) k_selftest(int op, int L, const uint32_t *x, int nx, long long ex,
+                                                    const uint32_t *y, int ny, long long ey, uint32_t *out,
+                                                    long long *eo, uint32_t *scr, long long *cs, int cap) {
+  __shared__ mp::Red red;
+  mp::Work w;
+  w.cs = cs;
+  w.tmp = scr + 3 * cap;
+  w.r = &red;
+  mp::NBufs B;
+  B.a = scr + 4 * cap;
+  B.b = scr + 5 * cap;
+  B.c = scr + 6 * cap;
+  B.d = scr + 7 * cap;
+  B.e = scr + 8 * cap;
+  B.f = scr + 9 * cap;
+  B.cap = cap;
+  uint32_t *big = scr + 10 * cap, *q = scr + 11 * cap, *xs = scr + 12 * cap, *V = scr + 13 * cap;
+  bool ok = true;
+  if (op == 0) {
+    mp::mul<NT_ST>(x, nx, y, ny, out, w);
+  } else if (op == 1) {
+    ok = mp::recip<NT_ST>(x, L, out, w, B);
+  } else if (op == 2) {
+    const mp::Rounded r = mp::sqrt_rne<NT_ST>(x, L, ex, out, w, B, big, xs, &ok);
+    if (threadIdx.x == 0) *eo = r.exp;
+  } else if (op == 3) {
+    ok = mp::recip<NT_ST>(y, L, V, w, B);
+    bool ok2 = true;
+    const mp::Rounded r = mp::div_rne<NT_ST>(x, ex, y, ey, V, L, out, w, big, q, &ok2);
+    ok = ok && ok2;
+    if (threadIdx.x == 0) *eo = r.exp;
+  } else if (op == 4) {
+    const mp::Rounded r = mp::round_rne<NT_ST>(x, nx, ex, L, out, w);
+    if (threadIdx.x == 0) *eo = r.nonzero ? r.exp : 0;
+  }
+  if (threadIdx.x == 0 && !ok) eo[1] = 1;
+}
+
+}  // namespace
+
+int selftest_mp(int op, int L, const uint32_t *x, int nx, int64_t ex, const uint32_t *y, int ny, int64_t ey,
+                uint32_t *out, int64_t *eo) {
+  if (L < 1 || nx < 0 || ny < 0 || op < 0 || op > 4) return 1;
+  const int cap = 5 * (nx + ny + L) + 128;
+  int nout = 0;
+  switch (op) {
+    case 0: nout = nx + ny + 2; break;
+    case 1: nout = L + 2; break;
+    default: nout = L; break;
+  }
+  uint32_t *dx = nullptr, *dy = nullptr, *dout = nullptr, *scr = nullptr;
+  long long *dcs = nullptr, *deo = nullptr;
+  int rc = 0;
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == 0) rc = 3;
+  };
+  ck(cudaMalloc(&dx, 4 * (size_t)(nx + 1)));
+  ck(cudaMalloc(&dy, 4 * (size_t)(ny + 1)));
+  ck(cudaMalloc(&dout, 4 * (size_t)(cap)));
+  ck(cudaMalloc(&scr, 4 * (size_t)cap * 14));
+  ck(cudaMalloc(&dcs, 8 * (size_t)cap));
+  ck(cudaMalloc(&deo, 16));
+  if (rc == 0) {
+    ck(cudaMemcpy(dx, x, 4 * (size_t)nx, cudaMemcpyHostToDevice));
+    if (ny) ck(cudaMemcpy(dy, y, 4 * (size_t)ny, cudaMemcpyHostToDevice));
+    ck(cudaMemset(deo, 0, 16));
+    ck(cudaMemset(dout, 0, 4 * (size_t)cap));
+    ck(cudaMemset(scr, 0, 4 * (size_t)cap * 14));
+    k_selftest<<<1, NT_ST>>>(op, L, dx, nx, ex, dy, ny, ey, dout, deo, scr, dcs, cap);
+    ck(cudaGetLastError());
+    ck(cudaDeviceSynchronize());
+    ck(cudaMemcpy(out, dout, 4 * (size_t)nout, cudaMemcpyDeviceToHost));
+    long long h[2] = {0, 0};
+    ck(cudaMemcpy(h, deo, 16, cudaMemcpyDeviceToHost));
+    eo[0] = h[0];
+    eo[1] = h[1];
+  }
+  cudaFree(dx);
+  cudaFree(dy);
+  cudaFree(dout);
+  cudaFree(scr);
+  cudaFree(dcs);
+  cudaFree(deo);
+  return rc;
+}
+
+}  // namespace hk

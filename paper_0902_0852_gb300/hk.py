@@ -1,0 +1,301 @@
+"""Thin Python binding of libhk (include/hk.h): argument marshalling only.
+
+Every step of the factorisation and of inverse iteration runs in the CUDA
+library; this module converts Python integers / numpy arrays / torch tensors to
+the flat C-ABI arrays and back.  It raises ``HKError`` for any non-zero status
+and ``RuntimeError`` when the compiled library is missing — there is no
+fallback.
+
+Values are exchanged as pairs ``(n, e)`` of Python ints meaning ``n * 2**e``
+(|n| a P-bit mantissa or 0), the same convention as the oracle.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libhk.so")
+_lib = None
+
+HK_OK, HK_ERR_ARG, HK_ERR_NOT_PD, HK_ERR_CUDA, HK_ERR_OOM, HK_ERR_TIMEOUT, HK_ERR_STATE, HK_ERR_RANGE = range(8)
+
+EXPORTS = [
+    "hk_create", "hk_destroy", "hk_strerror", "hk_workspace_bytes", "hk_set_workspace",
+    "hk_load_moments", "hk_load_moments_flat", "hk_factor", "hk_get_R", "hk_get_R_flat",
+    "hk_smallest_eig", "hk_get_history_flat", "hk_get_timings", "hk_get_stats", "hk_selftest_mp",
+]
+
+
+class HKError(RuntimeError):
+    def __init__(self, code, what, extra=None):
+        self.code = code
+        self.extra = extra
+        msg = lib().hk_strerror(code).decode()
+        super().__init__(f"{what}: {msg} (status {code})" + (f" [{extra}]" if extra is not None else ""))
+
+
+class HkMp(ctypes.Structure):
+    _fields_ = [("sign", ctypes.c_int32), ("exp", ctypes.c_int64), ("limbs", ctypes.POINTER(ctypes.c_uint32))]
+
+
+def lib():
+    """The loaded libhk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libhk.so not built ({_LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+        P32, P64, PU32 = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint32)
+        L.hk_create.argtypes = [ctypes.POINTER(vp), i32, vp]
+        L.hk_destroy.argtypes = [vp]
+        L.hk_destroy.restype = None
+        L.hk_strerror.argtypes = [i32]
+        L.hk_strerror.restype = ctypes.c_char_p
+        L.hk_workspace_bytes.argtypes = [i32, i32, ctypes.POINTER(sz)]
+        L.hk_set_workspace.argtypes = [vp, vp, sz]
+        L.hk_load_moments.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(HkMp)]
+        L.hk_load_moments_flat.argtypes = [vp, i32, i32, i32, i32, vp, vp, vp, i32]
+        L.hk_factor.argtypes = [vp, ctypes.POINTER(i32)]
+        L.hk_get_R.argtypes = [vp, ctypes.POINTER(HkMp)]
+        L.hk_get_R_flat.argtypes = [vp, vp, vp, vp]
+        L.hk_smallest_eig.argtypes = [vp, i32, ctypes.POINTER(HkMp), ctypes.POINTER(i32)]
+        L.hk_get_history_flat.argtypes = [vp, i32, vp, vp, vp]
+        L.hk_get_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32]
+        L.hk_get_stats.argtypes = [vp, P64, i32]
+        L.hk_selftest_mp.argtypes = [i32, i32, PU32, i32, i64, PU32, i32, i64, PU32, P64]
+        for name in EXPORTS:
+            getattr(L, name).restype = getattr(L, name).restype if name in ("hk_destroy", "hk_strerror") else i32
+        _lib = L
+    return _lib
+
+
+def _check(code, what, extra=None):
+    if code != HK_OK:
+        raise HKError(code, what, extra)
+
+
+# ---------------------------------------------------------------------------
+# marshalling of P-bit values
+# ---------------------------------------------------------------------------
+
+def pack(values, P):
+    """(n, e) pairs -> (sign int32[k], exp int64[k], limbs uint32[k, L])."""
+    L = P // 32
+    k = len(values)
+    sign = np.zeros(k, dtype=np.int32)
+    exp = np.zeros(k, dtype=np.int64)
+    buf = bytearray(4 * L * k)
+    for idx, (n, e) in enumerate(values):
+        if n == 0:
+            continue
+        a = -n if n < 0 else n
+        if a.bit_length() != P:
+            raise ValueError("mantissa is not normalised to P bits")
+        sign[idx] = 1 if n < 0 else 0
+        exp[idx] = e
+        buf[4 * L * idx: 4 * L * (idx + 1)] = a.to_bytes(4 * L, "little")
+    limbs = np.frombuffer(bytes(buf), dtype=np.uint32).reshape(k, L).copy()
+    return sign, exp, limbs
+
+
+def unpack(sign, exp, limbs):
+    """Inverse of ``pack``."""
+    limbs = np.ascontiguousarray(limbs, dtype=np.uint32)
+    out = []
+    raw = limbs.tobytes()
+    L = limbs.shape[-1]
+    for idx in range(len(sign)):
+        a = int.from_bytes(raw[4 * L * idx: 4 * L * (idx + 1)], "little")
+        if a == 0:
+            out.append((0, 0))
+        else:
+            out.append((-a if sign[idx] else a, int(exp[idx])))
+    return out
+
+
+def _ptr(a):
+    if hasattr(a, "data_ptr"):  # torch tensor (device memory)
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---------------------------------------------------------------------------
+# C-ABI mirrors
+# ---------------------------------------------------------------------------
+
+def hk_create(device=0, stream=None):
+    """``hk_create``; ``stream`` is a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    h = ctypes.c_void_p()
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+    _check(lib().hk_create(ctypes.byref(h), device, ctypes.c_void_p(s)), "hk_create")
+    return h
+
+
+def hk_destroy(ctx):
+    lib().hk_destroy(ctx)
+
+
+def hk_workspace_bytes(N, P):
+    b = ctypes.c_size_t()
+    _check(lib().hk_workspace_bytes(N, P, ctypes.byref(b)), "hk_workspace_bytes")
+    return b.value
+
+
+def hk_set_workspace(ctx, tensor):
+    """Use a caller-owned device buffer (e.g. a torch uint8 CUDA tensor)."""
+    _check(lib().hk_set_workspace(ctx, ctypes.c_void_p(tensor.data_ptr()), tensor.numel() * tensor.element_size()),
+           "hk_set_workspace")
+
+
+def hk_load_moments_flat(ctx, N, beta, P, sign, exp, limbs, on_device=False):
+    p, q = beta
+    _check(lib().hk_load_moments_flat(ctx, N, p, q, P, _ptr(sign), _ptr(exp), _ptr(limbs), 1 if on_device else 0),
+           "hk_load_moments_flat")
+
+
+def hk_load_moments(ctx, N, beta, P, moments):
+    """Host moments as (n, e) pairs through the struct-array entry point."""
+    sign, exp, limbs = pack(moments, P)
+    arr = (HkMp * len(moments))()
+    for k in range(len(moments)):
+        arr[k].sign = int(sign[k])
+        arr[k].exp = int(exp[k])
+        arr[k].limbs = limbs[k].ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+    p, q = beta
+    _check(lib().hk_load_moments(ctx, N, p, q, P, arr), "hk_load_moments")
+
+
+def hk_factor(ctx):
+    bad = ctypes.c_int(-1)
+    code = lib().hk_factor(ctx, ctypes.byref(bad))
+    if code == HK_ERR_NOT_PD:
+        raise HKError(code, "hk_factor", extra={"bad_row": bad.value})
+    _check(code, "hk_factor")
+
+
+def hk_get_R_flat(ctx, N, P):
+    L = P // 32
+    nt = N * (N + 1) // 2
+    sign = np.zeros(nt, dtype=np.int32)
+    exp = np.zeros(nt, dtype=np.int64)
+    limbs = np.zeros((nt, L), dtype=np.uint32)
+    _check(lib().hk_get_R_flat(ctx, _ptr(sign), _ptr(exp), _ptr(limbs)), "hk_get_R_flat")
+    return sign, exp, limbs
+
+
+def hk_get_R(ctx, N, P):
+    """R as rows of (n, e): ``R[t][j - t]`` = R_tj, like the oracle."""
+    vals = unpack(*hk_get_R_flat(ctx, N, P))
+    rows, k = [], 0
+    for t in range(N):
+        rows.append(vals[k:k + N - t])
+        k += N - t
+    return rows
+
+
+def hk_smallest_eig(ctx, P, iters):
+    L = P // 32
+    limbs = np.zeros(L, dtype=np.uint32)
+    m = HkMp(0, 0, limbs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    used = ctypes.c_int(0)
+    _check(lib().hk_smallest_eig(ctx, iters, ctypes.byref(m), ctypes.byref(used)), "hk_smallest_eig")
+    return unpack(np.array([m.sign]), np.array([m.exp]), limbs.reshape(1, L))[0], used.value
+
+
+def hk_get_history_flat(ctx, count, P):
+    L = P // 32
+    sign = np.zeros(count, dtype=np.int32)
+    exp = np.zeros(count, dtype=np.int64)
+    limbs = np.zeros((count, L), dtype=np.uint32)
+    _check(lib().hk_get_history_flat(ctx, count, _ptr(sign), _ptr(exp), _ptr(limbs)), "hk_get_history_flat")
+    return unpack(sign, exp, limbs)
+
+
+def hk_get_timings(ctx):
+    out = (ctypes.c_double * 5)()
+    _check(lib().hk_get_timings(ctx, out, 5), "hk_get_timings")
+    keys = ["update_ms", "panel_ms", "solve_ms", "factor_ms", "eig_ms"]
+    return dict(zip(keys, list(out)))
+
+
+def hk_get_stats(ctx):
+    out = (ctypes.c_int64 * 3)()
+    _check(lib().hk_get_stats(ctx, out, 3), "hk_get_stats")
+    return {"launches": out[0], "W": out[1], "widenings": out[2]}
+
+
+def hk_selftest_mp(op, L, x, ex=0, y=None, ey=0):
+    """Run one device multiprecision operation on Python-int operands.
+    op 0: x*y; 1: floor(2^(2P+1)/x); 2: RNE sqrt(x 2^ex); 3: RNE (x 2^ex)/(y 2^ey);
+    4: RNE(x 2^ex) (x an nx-limb integer).  Returns an int, or (mantissa, exp)."""
+    def limbs_of(v, n):
+        return np.frombuffer(v.to_bytes(4 * n, "little"), dtype=np.uint32).copy()
+    nx = max(1, (x.bit_length() + 31) // 32) if op in (0, 4) else L
+    xa = limbs_of(x, nx)
+    ny = 0
+    ya = np.zeros(1, dtype=np.uint32)
+    if y is not None:
+        ny = max(1, (y.bit_length() + 31) // 32) if op == 0 else L
+        ya = limbs_of(y, ny)
+    nout = {0: nx + ny + 2, 1: L + 2}.get(op, L)
+    out = np.zeros(max(nout, 1) + 8, dtype=np.uint32)
+    eo = np.zeros(2, dtype=np.int64)
+    PU32 = ctypes.POINTER(ctypes.c_uint32)
+    code = lib().hk_selftest_mp(op, L, xa.ctypes.data_as(PU32), nx, ex, ya.ctypes.data_as(PU32), ny, ey,
+                                out.ctypes.data_as(PU32), eo.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    _check(code, "hk_selftest_mp")
+    if eo[1]:
+        raise HKError(HK_ERR_TIMEOUT, "hk_selftest_mp correction did not settle")
+    val = int.from_bytes(out[:nout].tobytes(), "little")
+    if op in (0, 1):
+        return val
+    return val, int(eo[0])
+
+
+class Hankel:
+    """Convenience wrapper: one context, one problem."""
+
+    def __init__(self, device=0, stream=None):
+        self.ctx = hk_create(device, stream)
+        self.N = self.P = None
+
+    def close(self):
+        if self.ctx is not None:
+            hk_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def load(self, N, beta, P, moments):
+        self.N, self.P = N, P
+        sign, exp, limbs = pack(moments, P)
+        hk_load_moments_flat(self.ctx, N, beta, P, sign, exp, limbs)
+
+    def load_device(self, N, beta, P, sign, exp, limbs):
+        """Moments already resident in device memory (torch CUDA tensors)."""
+        self.N, self.P = N, P
+        hk_load_moments_flat(self.ctx, N, beta, P, sign, exp, limbs, on_device=True)
+
+    def factor(self):
+        hk_factor(self.ctx)
+
+    def R(self):
+        return hk_get_R(self.ctx, self.N, self.P)
+
+    def smallest_eig(self, iters):
+        return hk_smallest_eig(self.ctx, self.P, iters)
+
+    def history(self, count):
+        return hk_get_history_flat(self.ctx, count, self.P)
+
+    def timings(self):
+        return hk_get_timings(self.ctx)
+
+    def stats(self):
+        return hk_get_stats(self.ctx)

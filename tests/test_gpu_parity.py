@@ -1,0 +1,122 @@
+"""Bit-exact parity of the CUDA path with the oracle: R element by element,
+the inverse-iteration history lambda_1..lambda_T, and the degenerate cases.
+All inputs are the seeded moments of the paper's matrices (or of small
+explicit measures); the calls go through the C ABI."""
+import math
+from fractions import Fraction
+
+import pytest
+
+import oracle
+from paper_0902_0852_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hk():
+    from paper_0902_0852_gb300 import build, hk as mod
+    build.build()
+    mod.lib()
+    return mod
+
+
+def gpu_run(hk, N, beta, P, T, moments=None):
+    m = moments if moments is not None else inputs.moments(N, beta, P)
+    with hk.Hankel(0) as h:
+        h.load(N, beta, P, m)
+        h.factor()
+        R = h.R()
+        lam, hist = None, []
+        if T:
+            lam, used = h.smallest_eig(T)
+            assert used == T
+            hist = h.history(T)
+        stats = h.stats()
+    return m, R, lam, hist, stats
+
+
+@pytest.mark.parametrize("N,beta,P", [(1, (1, 1), 32), (2, (1, 1), 32), (3, (7, 4), 64), (4, (1, 1), 32),
+                                      (4, (7, 4), 128), (5, (3, 4), 64), (12, (7, 4), 256),
+                                      (17, (3, 2), 320), (20, (2, 1), 96)])
+def test_factor_small(hk, N, beta, P):
+    m, R, _, _, _ = gpu_run(hk, N, beta, P, 0)
+    assert R == oracle.cholesky(m, N, P)
+
+
+def test_factor_spans_several_blocks_and_tiles(hk):
+    """N = 40 crosses two 16-row panel blocks and a ragged third one."""
+    N, P = 40, 384
+    for beta in [(7, 4), (3, 1)]:
+        m, R, _, _, _ = gpu_run(hk, N, beta, P, 0)
+        assert R == oracle.cholesky(m, N, P), beta
+
+
+def test_config1_factor_and_lambda(hk):
+    """N = 64, beta = 1 (moments k!), P = 2048, T = 50 from the all-ones vector:
+    R equals the closed form i! C(i,k) and the oracle bit for bit, and so does
+    every lambda_t."""
+    N, P, T = 64, 2048, 50
+    m, R, lam, hist, _ = gpu_run(hk, N, (1, 1), P, T)
+    for k in range(N):
+        for i in range(k, N):
+            n, e = R[k][i - k]
+            assert Fraction(n) * Fraction(2) ** e == math.factorial(i) * math.comb(i, k)
+    Ro = oracle.cholesky(m, N, P)
+    assert R == Ro
+    lam_o, hist_o, _ = oracle.inverse_iteration(Ro, P, T)
+    assert hist == hist_o
+    assert lam == lam_o
+
+
+@pytest.mark.parametrize("N,beta,P,T", [(24, (7, 4), 512, 12), (30, (3, 4), 768, 10), (33, (1, 1), 640, 9)])
+def test_lambda_parity(hk, N, beta, P, T):
+    m, R, lam, hist, _ = gpu_run(hk, N, beta, P, T)
+    Ro = oracle.cholesky(m, N, P)
+    assert R == Ro
+    lam_o, hist_o, _ = oracle.inverse_iteration(Ro, P, T)
+    assert hist == hist_o
+
+
+def test_not_positive_definite_row(hk):
+    P = 32
+    m = [oracle.rne(v, 0, P) for v in (1, 2, 1)]  # [[1, 2], [2, 1]]
+    with hk.Hankel(0) as h:
+        h.load(2, (1, 1), P, m)
+        with pytest.raises(hk.HKError) as ei:
+            h.factor()
+    assert ei.value.code == hk.HK_ERR_NOT_PD and ei.value.extra["bad_row"] == 1
+
+
+def test_not_positive_definite_late_row(hk):
+    """A PD leading block followed by a failing pivot: same row as the oracle."""
+    P, N = 64, 6
+    base = inputs.moments(N, (1, 1), P)
+    m = list(base)
+    m[8] = oracle.rne(1, 0, P)  # m_8 = 1 makes S_44 negative
+    with pytest.raises(oracle.NotPositiveDefinite) as eo:
+        oracle.cholesky(m, N, P)
+    with hk.Hankel(0) as h:
+        h.load(N, (1, 1), P, m)
+        with pytest.raises(hk.HKError) as ei:
+            h.factor()
+    assert ei.value.extra["bad_row"] == eo.value.row
+
+
+def test_signed_entries(hk):
+    """Moments of a measure with negative support points: negative R entries
+    exercise the subtracting branch of the update kernel."""
+    pts = [(-3, 2), (-1, 2), (Fraction(1, 2), 1), (2, 1), (-5, 1), (-Fraction(3, 2), 2), (4, 1), (-7, 1)]
+    N, P = 8, 192
+    mom = []
+    for k in range(2 * N - 1):
+        v = sum((w * Fraction(x) ** k for x, w in pts), Fraction(0))
+        n, d = v.numerator, v.denominator
+        # round v to P bits (exact rational rounding through the oracle's division)
+        mom.append(oracle.mp_div(oracle.rne(n, 0, P * 4), oracle.rne(d, 0, P * 4), P) if n else (0, 0))
+    m, R, lam, hist, _ = gpu_run(hk, N, (1, 1), P, 6, moments=mom)
+    Ro = oracle.cholesky(mom, N, P)
+    assert any(x[0] < 0 for row in Ro for x in row)
+    assert R == Ro
+    _, hist_o, _ = oracle.inverse_iteration(Ro, P, 6)
+    assert hist == hist_o
