@@ -1,0 +1,333 @@
+#!/usr/bin/env python3
+"""Benchmark: P-bit multiply-accumulates per second of the exact Cholesky
+factorisation + inverse iteration of the Hankel moment matrix, and the time
+to lambda_min, at the paper-scale workload N = 1000, beta = 1, P = 24576 bits.
+
+One step = load the 2N-1 moments (already resident in device memory),
+factor M = R^T R, run inverse iteration until |lambda_t - lambda_{t-1}| <=
+2^-136 lambda_t.  The e2e leg repeats the step through the C ABI from pinned
+host buffers (host->device moments and device->host lambda inside the timed
+region).  `--impl reference` times the CPU oracle on a bounded sample of the
+same workload.
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas
+(one instance per GPU; the single-instance factorisation does not shard).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "P-bit MAC/s in Cholesky update (+ inverse iteration), time-to-lambda_min"
+UNIT = "MAC/s"
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+# DRAM bytes (read + write) per limb product of the update kernel, from one ncu
+# capture of the current kernel version (see profiles/); None when not measured.
+UPDATE_TRAFFIC_BYTES_PER_LIMBPROD = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--N", type=int, default=1000)
+    ap.add_argument("--P", type=int, default=24576)
+    ap.add_argument("--iters", type=int, default=0, help="0 = until converged (2^-136)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def step_macs(N, T):
+    """Algorithmic P-bit MACs: factor (N-1)N(N+1)/6, two solves of N(N-1)/2
+    per inverse-iteration step, and the two dot products (2N)."""
+    return (N - 1) * N * (N + 1) // 6 + T * (N * (N - 1) + 2 * N)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+
+def _oracle_chunk(args):
+    import oracle
+    i, moments, col_i, cols, P = args
+    oracle.cholesky_row(i, moments, col_i, cols, P)
+    return sum(len(c) for c in cols.values())
+
+
+def oracle_sample_setup(N, P, row):
+    """Inputs of one row of the beta = 1 factorisation: the rows above it are
+    the exact closed form i! C(i, k) (equal to the oracle's own rows at this P)."""
+    from math import comb, factorial
+    import oracle
+    from paper_0902_0852_gb300 import inputs
+    m = inputs.moments(N, (1, 1), P)
+    fact = [factorial(k) for k in range(N)]
+    col = {j: [oracle.rne(fact[j] * comb(j, t), 0, P) for t in range(row)] for j in range(row, N)}
+    return m, col
+
+
+def oracle_sample(pool, cores, N, P, row, setup):
+    """Time row `row` (all columns) of the oracle factorisation; returns
+    (MACs, seconds)."""
+    m, col = setup
+    js = list(range(row, N))
+    chunks = [js[k::cores] for k in range(cores)]
+    tasks = [(row, m, col[row], {j: col[j] for j in ch}, P) for ch in chunks if ch]
+    t0 = time.perf_counter()
+    macs = sum(pool.map(_oracle_chunk, tasks))
+    return macs, time.perf_counter() - t0
+
+
+def make_pool(cores):
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    pool = ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"))
+    list(pool.map(abs, range(cores)))  # start the workers
+    return pool
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    def __init__(self, dev):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={SMI_FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(dev)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    N, P, row = args.N, args.P, args.N // 2
+    cores = os.cpu_count() or 1
+    pool = make_pool(cores)
+    setup = oracle_sample_setup(N, P, row)
+    for _ in range(args.warmup):
+        oracle_sample(pool, cores, N, P, row, setup)
+    tot_m, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        m, t = oracle_sample(pool, cores, N, P, row, setup)
+        tot_m += m
+        tot_t += t
+    pool.shutdown()
+    v = tot_m / tot_t
+    sample = f"row {row} of the N={N}, P={P}, beta=1 factorisation ({N - row} entries, {tot_m // args.steps} MACs per step)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "python-int (exact)",
+        "data": "synthetic",
+        "config": {"workload": f"Hankel moment matrix N={N}, beta=1 (m_k = k!), P={P} bits; oracle sample", "N": N,
+                   "P": P, "beta": "1"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    N, P, beta = args.N, args.P, (1, 1)
+    L = P // 32
+
+    # the CPU baseline first (spawn pool, before any CUDA work)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        row = N // 2
+        pool = make_pool(cores)
+        setup = oracle_sample_setup(N, P, row)
+        m_, t_ = oracle_sample(pool, cores, N, P, row, setup)
+        pool.shutdown()
+        cpu = {"value": m_ / t_, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"row {row} of the N={N}, P={P}, beta=1 factorisation ({N - row} entries, {m_} MACs, "
+                         f"{t_:.1f} s)"}
+
+    import numpy as np
+    import torch
+    from paper_0902_0852_gb300 import build, hk, inputs
+    build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    stream = torch.cuda.current_stream()
+    moments = inputs.moments(N, beta, P)
+    s_h, e_h, l_h = hk.pack(moments, P)
+    s_d = torch.from_numpy(s_h).cuda()
+    e_d = torch.from_numpy(e_h).cuda()
+    l_d = torch.from_numpy(l_h.view(np.int32)).cuda()
+    # pinned host copies for the e2e leg
+    s_p = torch.from_numpy(s_h).pin_memory()
+    e_p = torch.from_numpy(e_h).pin_memory()
+    l_p = torch.from_numpy(l_h.view(np.int32)).pin_memory()
+    h2d = s_h.nbytes + e_h.nbytes + l_h.nbytes
+    d2h = 4 * L + 12
+
+    h = hk.Hankel(local, stream)
+    peaks = hk.hk_probe_int_peaks(local)
+
+    def step(device_inputs):
+        if device_inputs:
+            h.load_device(N, beta, P, s_d, e_d, l_d)
+        else:
+            hk.hk_load_moments_flat(h.ctx, N, beta, P, s_p, e_p, l_p, on_device=False)
+        h.factor()
+        lam, used = h.smallest_eig(args.iters)
+        return lam, used, h.timings(), h.stats()
+
+    for _ in range(args.warmup):
+        step(True)
+    torch.cuda.synchronize()
+
+    # ---- timed: device-resident inputs ----
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    recs = [step(True) for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    t_dev = ev0.elapsed_time(ev1) / 1e3
+
+    # ---- timed: end to end from pinned host buffers ----
+    barrier()
+    torch.cuda.synchronize()
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ee0.record(stream)
+    recs_e2e = [step(False) for _ in range(args.steps)]
+    ee1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_e2e = ee0.elapsed_time(ee1) / 1e3
+
+    lam, used = recs[-1][0], recs[-1][1]
+    if lam != recs_e2e[-1][0]:
+        raise SystemExit("device-resident and end-to-end runs disagree on lambda")
+    macs = sum(step_macs(N, r[1]) for r in recs)
+    macs_e2e = sum(step_macs(N, r[1]) for r in recs_e2e)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_dev, t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev, t_e2e = float(t[0]), float(t[1])
+        m = torch.tensor([macs, macs_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(m, op=dist.ReduceOp.SUM)
+        macs, macs_e2e = float(m[0]), float(m[1])
+    if rank != 0:
+        h.close()
+        return
+
+    # roofline of the update kernel (factor launches), CUDA events per launch
+    upd_ms = sum(r[2]["update_ms"] for r in recs)
+    fac_ms = sum(r[2]["factor_ms"] for r in recs)
+    eig_ms = sum(r[2]["eig_ms"] for r in recs)
+    limbprod = (N - 1) * N * (N + 1) // 6 * L * L * args.steps
+    achieved = limbprod / (upd_ms / 1e3) / 1e12
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = n_sm * 64 * max_mhz * 1e6 / 2 / 1e12
+    traffic = (UPDATE_TRAFFIC_BYTES_PER_LIMBPROD * limbprod / args.steps /
+               (recs[-1][3]["launches"] or 1)) if UPDATE_TRAFFIC_BYTES_PER_LIMBPROD else None
+    n_lam, e_lam = lam
+    # decimal rendering of lambda (n * 2^e) with 10 significant digits
+    lg = math.log10(abs(n_lam)) + e_lam * math.log10(2)
+    ex = math.floor(lg)
+    lam_str = f"{10 ** (lg - ex):.9f}e{ex}"
+
+    out = {
+        "metric": METRIC, "value": macs / t_dev, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"Hankel moment matrix N={N}, beta=1 (m_k = k!), P={P} bits (L={L}); Cholesky + "
+                               f"inverse iteration to 2^-136", "N": N, "beta": "1", "P": P,
+                   "iters": "converged" if args.iters == 0 else args.iters,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "no flush: working set (R and its aligned copy, 3.2 GB) is far larger than L2"},
+        "time_to_lambda_s": t_dev / args.steps, "iters_used": used, "lambda_min": lam_str,
+        "lambda_min_table3": "1.0892e-52" if (N, P) == (1000, 24576) else None,
+        "factor_ms": fac_ms / args.steps, "inverse_iteration_ms": eig_ms / args.steps,
+        "factor_macs_per_s": (N - 1) * N * (N + 1) / 6 / (fac_ms / args.steps / 1e3),
+        "limb_products_per_s_factor": limbprod / args.steps / (fac_ms / args.steps / 1e3),
+        "e2e": {"value": macs_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlimbprod/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_update (exact trailing update), factor launches",
+                     "peak_basis": f"{n_sm} SMs x 64 IMAD/clk/SM x {max_mhz:.0f} MHz / 2 IMAD per 32x32->64 "
+                                   f"limb product (probe: {peaks['imad_per_clk_sm']:.1f} IMAD/clk/SM)"},
+        "int_probe": peaks,
+        "clocks": clocks,
+        "gpu_launches": sum(r[3]["launches"] for r in recs),
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    h.close()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -135,6 +135,16 @@ int hk_get_timings(hk_ctx *ctx, double *out, int n);
  * widenings taken. */
 int hk_get_stats(hk_ctx *ctx, int64_t *out, int n);
 
+/* ----- measurement hook ------------------------------------------------------
+ * Integer throughput of the device (a few ms on every SM): out[0] IMAD
+ * (mad.lo.u32) per clock per SM and out[1] the SM clock in MHz seen by that
+ * probe; out[2] exact 32x32->64 limb products per clock per SM in the 3-word
+ * accumulation form of the update kernel (mad.lo.cc/madc.hi.cc/addc), out[3]
+ * its clock; out[4] u8 multiply-adds per clock per SM of mma.sync m16n8k32
+ * (the warp-level INT8 tensor instruction), out[5] its clock.  n >= 6.
+ * There is no counterpart in the paper: it measures the roofline denominator. */
+int hk_probe_int_peaks(int device, double *out, int n);
+
 /* ----- self-test hooks of the device multiprecision library ----------------
  * Run one single-CTA device operation on host operands (copied in and out) so
  * that tests can compare it with exact integer arithmetic:

@@ -69,6 +69,7 @@ struct hk_ctx {
   int32_t *Asign = nullptr;
   uint32_t *recip = nullptr;
   long long *colsum = nullptr;
+  int fac_N = 0, fac_L = 0, fac_W = 0;  // shape the factor buffers were allocated for
   std::map<std::pair<int, int>, std::pair<Unit *, int>> unit_cache;
   // solve buffers
   MpArr v{}, y{}, w{}, hist{};
@@ -221,16 +222,23 @@ __global__ void k_col_grid(int N, const long long *colU, int W, long long *colG)
 // one attempt of the blocked factorisation with window width c->W
 int factor_attempt(hk_ctx *c) {
   const int N = c->N, L = c->L, W = c->W, nb = c->nb;
-  c->fac_arena.release();
-  c->unit_cache.clear();
   const size_t NT = (size_t)N * (N + 1) / 2;
-  CK(alloc_mp(c, c->fac_arena, &c->R, NT, L));
-  CK(alloc(c, c->fac_arena, &c->A, NT * (size_t)W));
-  CK(alloc(c, c->fac_arena, &c->Asign, NT));
-  CK(alloc(c, c->fac_arena, &c->recip, (size_t)N * (L + 2)));
   c->C = colsum_width(W, W);
   const long long maxout = rows_outputs(N, 0, std::min(nb, N));
-  CK(alloc(c, c->fac_arena, &c->colsum, (size_t)maxout * c->C));
+  if (c->fac_N != N || c->fac_L != L || c->fac_W != W) {
+    // (re)allocate only when the shape changed; in caller-workspace mode the
+    // bump arena keeps the old region (a widening costs one more copy)
+    c->fac_arena.release();
+    c->fac_N = c->fac_L = c->fac_W = 0;
+    CK(alloc_mp(c, c->fac_arena, &c->R, NT, L));
+    CK(alloc(c, c->fac_arena, &c->A, NT * (size_t)W));
+    CK(alloc(c, c->fac_arena, &c->Asign, NT));
+    CK(alloc(c, c->fac_arena, &c->recip, (size_t)N * (L + 2)));
+    CK(alloc(c, c->fac_arena, &c->colsum, (size_t)maxout * c->C));
+    c->fac_N = N;
+    c->fac_L = L;
+    c->fac_W = W;
+  }
   Unit *units = nullptr;
   int nunits = 0;
   CK(units_for(c, W, W, &units, &nunits));
@@ -681,6 +689,8 @@ int hk_set_workspace(hk_ctx *c, void *dev_ptr, size_t bytes) {
   c->hist_cap = 0;
   c->vec_cap = 0;
   c->colsum_s_cap = 0;
+  c->fac_N = c->fac_L = c->fac_W = 0;
+  c->mom = MpArr{};
   c->unit_cache.clear();
   return HK_OK;
 }
@@ -703,30 +713,36 @@ int hk_load_moments_flat(hk_ctx *c, int N, int bnum, int bden, int P, const int3
     }
   }
   cudaStreamSynchronize(c->stream);
-  c->sol_arena.release();
-  c->fac_arena.release();
-  c->base_arena.release();
-  if (c->ws) {
-    c->base_arena.base = c->ws;
-    c->base_arena.cap = c->ws_bytes;
-    c->base_arena.used = 0;
-  }
-  c->unit_cache.clear();
-  c->loaded = c->factored = c->sol_ready = false;
-  c->hist_cap = 0;
+  const bool same = c->mom.limbs != nullptr && c->N == N && c->P == P;
+  c->loaded = c->factored = false;
   c->hist_count = 0;
-  c->vec_cap = 0;
-  c->colsum_s_cap = 0;
-  c->N = N;
-  c->L = L;
-  c->P = P;
   c->bnum = bnum;
   c->bden = bden;
-  CK(alloc_mp(c, c->base_arena, &c->mom, M, L));
-  CK(alloc(c, c->base_arena, &c->colU, (size_t)N));
-  CK(alloc(c, c->base_arena, &c->colG, (size_t)N));
-  CK(alloc(c, c->base_arena, &c->st, 1));
-  CK(alloc(c, c->base_arena, &c->d_range, 2));
+  if (!same) {
+    c->sol_arena.release();
+    c->fac_arena.release();
+    c->base_arena.release();
+    if (c->ws) {
+      c->base_arena.base = c->ws;
+      c->base_arena.cap = c->ws_bytes;
+      c->base_arena.used = 0;
+    }
+    c->unit_cache.clear();
+    c->sol_ready = false;
+    c->hist_cap = 0;
+    c->vec_cap = 0;
+    c->colsum_s_cap = 0;
+    c->fac_N = c->fac_L = c->fac_W = 0;
+    c->mom = MpArr{};
+    c->N = N;
+    c->L = L;
+    c->P = P;
+    CK(alloc_mp(c, c->base_arena, &c->mom, M, L));
+    CK(alloc(c, c->base_arena, &c->colU, (size_t)N));
+    CK(alloc(c, c->base_arena, &c->colG, (size_t)N));
+    CK(alloc(c, c->base_arena, &c->st, 1));
+    CK(alloc(c, c->base_arena, &c->d_range, 2));
+  }
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CK(cudaMemcpyAsync(c->mom.sign, sign, sizeof(int32_t) * M, kind, c->stream));
   CK(cudaMemcpyAsync(c->mom.exp, exp, sizeof(long long) * M, kind, c->stream));
@@ -756,11 +772,6 @@ int hk_factor(hk_ctx *c, int *bad_row) {
   if (!c->loaded) return HK_ERR_STATE;
   cudaSetDevice(c->device);
   c->factored = false;
-  c->sol_ready = false;
-  c->sol_arena.release();
-  c->hist_cap = 0;
-  c->vec_cap = 0;
-  c->colsum_s_cap = 0;
   c->launches = 0;
   c->widenings = 0;
   c->t_phase[0] = c->t_phase[1] = c->t_phase[2] = 0;

@@ -24,6 +24,7 @@ EXPORTS = [
     "hk_create", "hk_destroy", "hk_strerror", "hk_workspace_bytes", "hk_set_workspace",
     "hk_load_moments", "hk_load_moments_flat", "hk_factor", "hk_get_R", "hk_get_R_flat",
     "hk_smallest_eig", "hk_get_history_flat", "hk_get_timings", "hk_get_stats", "hk_selftest_mp",
+    "hk_probe_int_peaks",
 ]
 
 
@@ -65,6 +66,7 @@ def lib():
         L.hk_get_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32]
         L.hk_get_stats.argtypes = [vp, P64, i32]
         L.hk_selftest_mp.argtypes = [i32, i32, PU32, i32, i64, PU32, i32, i64, PU32, P64]
+        L.hk_probe_int_peaks.argtypes = [i32, ctypes.POINTER(ctypes.c_double), i32]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype if name in ("hk_destroy", "hk_strerror") else i32
         _lib = L
@@ -252,6 +254,14 @@ def hk_selftest_mp(op, L, x, ex=0, y=None, ey=0):
     if op in (0, 1):
         return val
     return val, int(eo[0])
+
+
+def hk_probe_int_peaks(device=0):
+    """Measured integer rates per clock per SM (see include/hk.h)."""
+    out = (ctypes.c_double * 6)()
+    _check(lib().hk_probe_int_peaks(device, out, 6), "hk_probe_int_peaks")
+    return {"imad_per_clk_sm": out[0], "imad_mhz": out[1], "limbprod_per_clk_sm": out[2],
+            "limbprod_mhz": out[3], "mma_u8_mac_per_clk_sm": out[4], "mma_mhz": out[5]}
 
 
 class Hankel:
