@@ -157,6 +157,31 @@ int hk_probe_int_peaks(int device, double *out, int n);
 int hk_selftest_mp(int op, int L, const uint32_t *x, int nx, int64_t ex,
                    const uint32_t *y, int ny, int64_t ey, uint32_t *out, int64_t *eo);
 
+/* ----- allocation-free multiprecision operation ----------------------------
+ * The paper has no counterpart: this is a service for callers that must not
+ * allocate device memory -- code whose device memory is owned by another
+ * allocator (a framework's caching allocator holding the whole budget), or
+ * latency-sensitive loops in which cudaMalloc/cudaFree would add implicit
+ * device synchronisation.  Same operations and op codes as hk_selftest_mp,
+ * but x, y, out and eo are DEVICE pointers and the work runs asynchronously
+ * on `stream` (a cudaStream_t, NULL = legacy default stream); the results are
+ * valid once the stream reaches this point.  out needs nx+ny+2 limbs (op 0),
+ * L+2 (op 1) or L (ops 2-4); eo needs 2 int64 (exponent, and 1 if an exact
+ * correction did not settle).  For ops 1 and 2, nx = L; for op 3, nx = ny = L.
+ *
+ * No memory is allocated: the work area is one fixed device array of about
+ * 1.3 MB inside the library (every GPU that loads the library holds it until
+ * the process exits), so sizes are limited to nx + ny + L <= 4096 limbs;
+ * larger requests return HK_ERR_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU (concurrent streams or host threads)
+ * race and must be serialised by the caller.  Each call clears the part of the
+ * array it uses before its kernel runs. */
+int hk_mp_op_noalloc(int op, int L, const uint32_t *x, int nx, int64_t ex,
+                     const uint32_t *y, int ny, int64_t ey, uint32_t *out, int64_t *eo,
+                     void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,7 +1,9 @@
 // Single-block driver of the device multiprecision library for unit tests:
 // operands and work areas live in global memory, one operation per launch.
+#include "hk.h"
 #include "hk_internal.h"
 #include "hk_mp.cuh"
+#include <mutex>
 #include <vector>
 
 namespace hk {
@@ -97,3 +99,61 @@ int selftest_mp(int op, int L, const uint32_t *x, int nx, int64_t ex, const uint
 }
 
 }  // namespace hk
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant: the same single-block operation on caller device
+// buffers, with its work area in a fixed device array instead of cudaMalloc.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int NOALLOC_MAX_LIMBS = 4096;                    // nx + ny + L
+constexpr int NOALLOC_CAP = 5 * NOALLOC_MAX_LIMBS + 128;   // limbs per work buffer
+constexpr size_t NOALLOC_BYTES = (size_t)NOALLOC_CAP * (14 * 4 + 8);
+
+// Work area shared by every call on a device; lives until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_ptr[MAX_DEVICES] = {};
+
+// device address of the work area for the current device (set up once per
+// device, with that device current)
+cudaError_t noalloc_area(unsigned char **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = reinterpret_cast<unsigned char *>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int hk_mp_op_noalloc(int op, int L, const uint32_t *x, int nx, int64_t ex, const uint32_t *y, int ny,
+                                int64_t ey, uint32_t *out, int64_t *eo, void *stream) {
+  if (L < 1 || nx < 0 || ny < 0 || op < 0 || op > 4 || !x || !out || !eo || (ny > 0 && !y))
+    return HK_ERR_ARG;
+  if ((op == 1 || op == 2) && nx != L) return HK_ERR_ARG;
+  if (op == 3 && (nx != L || ny != L)) return HK_ERR_ARG;
+  if (nx + ny + L > NOALLOC_MAX_LIMBS) return HK_ERR_ARG;
+  unsigned char *area = nullptr;
+  if (noalloc_area(&area) != cudaSuccess) return HK_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int cap = 5 * (nx + ny + L) + 128;
+  uint32_t *scr = reinterpret_cast<uint32_t *>(area);
+  long long *cs = reinterpret_cast<long long *>(area + (size_t)NOALLOC_CAP * 14 * 4);
+  // the allocating entry point starts from zeroed work buffers and exponent words
+  if (cudaMemsetAsync(scr, 0, 4 * (size_t)cap * 14, s) != cudaSuccess) return HK_ERR_CUDA;
+  if (cudaMemsetAsync(eo, 0, 2 * sizeof(int64_t), s) != cudaSuccess) return HK_ERR_CUDA;
+  hk::k_selftest<<<1, hk::NT_ST, 0, s>>>(op, L, x, nx, ex, ny ? y : x, ny, ey, out,
+                                          reinterpret_cast<long long *>(eo), scr, cs, cap);
+  return cudaGetLastError() == cudaSuccess ? HK_OK : HK_ERR_CUDA;
+}

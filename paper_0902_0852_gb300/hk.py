@@ -24,7 +24,7 @@ EXPORTS = [
     "hk_create", "hk_destroy", "hk_strerror", "hk_workspace_bytes", "hk_set_workspace",
     "hk_load_moments", "hk_load_moments_flat", "hk_factor", "hk_get_R", "hk_get_R_flat",
     "hk_smallest_eig", "hk_get_history_flat", "hk_get_timings", "hk_get_stats", "hk_selftest_mp",
-    "hk_probe_int_peaks",
+    "hk_probe_int_peaks", "hk_mp_op_noalloc",
 ]
 
 
@@ -67,6 +67,7 @@ def lib():
         L.hk_get_stats.argtypes = [vp, P64, i32]
         L.hk_selftest_mp.argtypes = [i32, i32, PU32, i32, i64, PU32, i32, i64, PU32, P64]
         L.hk_probe_int_peaks.argtypes = [i32, ctypes.POINTER(ctypes.c_double), i32]
+        L.hk_mp_op_noalloc.argtypes = [i32, i32, vp, i32, i64, vp, i32, i64, vp, vp, vp]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype if name in ("hk_destroy", "hk_strerror") else i32
         _lib = L
@@ -262,6 +263,18 @@ def hk_probe_int_peaks(device=0):
     _check(lib().hk_probe_int_peaks(device, out, 6), "hk_probe_int_peaks")
     return {"imad_per_clk_sm": out[0], "imad_mhz": out[1], "limbprod_per_clk_sm": out[2],
             "limbprod_mhz": out[3], "mma_u8_mac_per_clk_sm": out[4], "mma_mhz": out[5]}
+
+
+def hk_mp_op_noalloc(op, L, x, ex, y, ey, out, eo, stream=None):
+    """Allocation-free device operation: x, y, out, eo are CUDA tensors
+    (uint32 limbs viewed as int32, eo int64[2]); asynchronous on ``stream``."""
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+    nx = x.numel()
+    ny = 0 if y is None else y.numel()
+    yp = ctypes.c_void_p(y.data_ptr()) if y is not None else ctypes.c_void_p(0)
+    _check(lib().hk_mp_op_noalloc(op, L, ctypes.c_void_p(x.data_ptr()), nx, ex, yp, ny, ey,
+                                  ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(eo.data_ptr()),
+                                  ctypes.c_void_p(s)), "hk_mp_op_noalloc")
 
 
 class Hankel:
