@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -47,6 +48,19 @@ struct EvPair {
   cudaEvent_t a, b;
 };
 
+// unit table and schedule of the update kernel for one operand shape
+struct Sched {
+  Unit *units;
+  int n, uc, upc;
+  int nsub;
+  SubProb sub[MAX_SUB];
+  int C;  // column sums per output
+};
+
+// gap between Karatsuba pieces: covers the zero padding a unit reads past a
+// piece (stripe width + chunk length)
+constexpr int KAR_GAP = 64;
+
 }  // namespace
 
 struct hk_ctx {
@@ -66,11 +80,14 @@ struct hk_ctx {
   // factor buffers
   MpArr R{};
   uint32_t *A = nullptr;
+  uint32_t *Aexp = nullptr;  // Karatsuba expansion of A (levels > 0)
+  KarLayout kl{};
+  int kar_levels = 2;
   int32_t *Asign = nullptr;
   uint32_t *recip = nullptr;
   long long *colsum = nullptr;
-  int fac_N = 0, fac_L = 0, fac_W = 0;  // shape the factor buffers were allocated for
-  std::map<std::pair<int, int>, std::pair<Unit *, int>> unit_cache;
+  int fac_N = 0, fac_L = 0, fac_W = 0, fac_levels = -1;  // shape of the factor buffers
+  std::map<std::pair<long long, long long>, Sched> sched_cache;
   // solve buffers
   MpArr v{}, y{}, w{}, hist{};
   int hist_cap = 0, hist_count = 0;
@@ -158,26 +175,52 @@ void ev_collect(hk_ctx *c) {
   c->evused = 0;
 }
 
-cudaError_t units_for(hk_ctx *c, int Wx, int Wy, Unit **u, int *n) {
-  auto key = std::make_pair(Wx, Wy);
-  auto it = c->unit_cache.find(key);
-  if (it != c->unit_cache.end()) {
-    *u = it->second.first;
-    *n = it->second.second;
+// schedule of an update launch: the Karatsuba-expanded factor update
+// (levels > 0) or a plain contraction of widths (Wx, Wy)
+cudaError_t sched_for(hk_ctx *c, int Wx, int Wy, int levels, Sched *out) {
+  const auto key = std::make_pair((long long)Wx * 4096 + Wy, (long long)levels);
+  auto it = c->sched_cache.find(key);
+  if (it != c->sched_cache.end()) {
+    *out = it->second;
     return cudaSuccess;
   }
-  const int cnt = build_units(Wx, Wy, nullptr, 0);
-  std::vector<Unit> h(cnt);
-  build_units(Wx, Wy, h.data(), cnt);
-  Unit *d = nullptr;
-  cudaError_t e = alloc(c, c->base_arena, &d, (size_t)cnt);
+  Sched sc{};
+  int upc_cap = 8 * UC_MAX;
+  if (levels > 0) {
+    KarLayout kl;
+    kar_layout(Wx, levels, KAR_GAP, &kl);
+    sc.nsub = kar_subprobs(kl, sc.sub);
+    upc_cap = kl.G - 11;  // a unit may read up to stripe + chunk limbs past its piece
+  } else {
+    sc.nsub = 1;
+    sc.sub[0] = SubProb{};
+    sc.sub[0].wx = Wx;
+    sc.sub[0].wy = Wy;
+    sc.sub[0].nterm = 1;
+    sc.sub[0].tsign[0] = 1;
+  }
+  choose_schedule(sc.sub, sc.nsub, upc_cap, &sc.uc, &sc.upc);
+  sc.C = std::max(colsum_width(sc.sub, sc.nsub, sc.uc), ((Wx + Wy + 8 + 3) / 4) * 4);
+  sc.n = build_units(sc.sub, sc.nsub, sc.uc, sc.upc, nullptr, 0);
+  std::vector<Unit> h(sc.n);
+  build_units(sc.sub, sc.nsub, sc.uc, sc.upc, h.data(), sc.n);
+  cudaError_t e = alloc(c, c->base_arena, &sc.units, (size_t)sc.n);
   if (e != cudaSuccess) return e;
-  e = cudaMemcpy(d, h.data(), sizeof(Unit) * cnt, cudaMemcpyHostToDevice);
+  e = cudaMemcpy(sc.units, h.data(), sizeof(Unit) * sc.n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
-  c->unit_cache[key] = std::make_pair(d, cnt);
-  *u = d;
-  *n = cnt;
+  c->sched_cache[key] = sc;
+  *out = sc;
   return cudaSuccess;
+}
+
+void fill_sched(UpdParams &up, const Sched &sc) {
+  up.units = sc.units;
+  up.nunits = sc.n;
+  up.uc = sc.uc;
+  up.upc = sc.upc;
+  up.nsub = sc.nsub;
+  for (int k = 0; k < sc.nsub; k++) up.sub[k] = sc.sub[k];
+  up.C = sc.C;
 }
 
 int sm_count(hk_ctx *c) {
@@ -223,9 +266,13 @@ __global__ void k_col_grid(int N, const long long *colU, int W, long long *colG)
 int factor_attempt(hk_ctx *c) {
   const int N = c->N, L = c->L, W = c->W, nb = c->nb;
   const size_t NT = (size_t)N * (N + 1) / 2;
-  c->C = colsum_width(W, W);
+  const int levels = c->kar_levels;
+  kar_layout(W, levels, KAR_GAP, &c->kl);
+  Sched sc;
+  CK(sched_for(c, W, W, levels, &sc));
+  c->C = sc.C;
   const long long maxout = rows_outputs(N, 0, std::min(nb, N));
-  if (c->fac_N != N || c->fac_L != L || c->fac_W != W) {
+  if (c->fac_N != N || c->fac_L != L || c->fac_W != W || c->fac_levels != levels) {
     // (re)allocate only when the shape changed; in caller-workspace mode the
     // bump arena keeps the old region (a widening costs one more copy)
     c->fac_arena.release();
@@ -235,13 +282,13 @@ int factor_attempt(hk_ctx *c) {
     CK(alloc(c, c->fac_arena, &c->Asign, NT));
     CK(alloc(c, c->fac_arena, &c->recip, (size_t)N * (L + 2)));
     CK(alloc(c, c->fac_arena, &c->colsum, (size_t)maxout * c->C));
+    c->Aexp = nullptr;
+    if (levels > 0) CK(alloc(c, c->fac_arena, &c->Aexp, NT * (size_t)c->kl.stride));
     c->fac_N = N;
     c->fac_L = L;
     c->fac_W = W;
+    c->fac_levels = levels;
   }
-  Unit *units = nullptr;
-  int nunits = 0;
-  CK(units_for(c, W, W, &units, &nunits));
   CK(reset_status(c));
   CK(launch_col_tops(N, L, c->top_margin, c->mom, c->colU, c->st, c->stream));
   k_col_grid<<<(N + 127) / 128, 128, 0, c->stream>>>(N, c->colU, W, c->colG);
@@ -261,22 +308,21 @@ int factor_attempt(hk_ctx *c) {
   pp.recip = c->recip;
   pp.colsum = c->colsum;
   pp.st = c->st;
+  pp.kl = c->kl;
+  pp.Aexp = c->Aexp;
 
   UpdParams up;
   std::memset(&up, 0, sizeof(up));
   up.mode = M_FACTOR;
   up.N = N;
-  up.A = c->A;
+  up.A = levels > 0 ? c->Aexp : c->A;
   up.Asign = c->Asign;
-  up.W = W;
-  up.Wx = W;
-  up.Wy = W;
+  up.astride = levels > 0 ? c->kl.stride : W;
+  up.cx = up.cy = up.astride;
   up.colsum = c->colsum;
-  up.C = c->C;
-  up.units = units;
-  up.nunits = nunits;
+  fill_sched(up, sc);
   up.st = c->st;
-  const long long cta_per_out = (nunits + UNT - 1) / UNT;
+  const long long cta_per_out = (sc.n + UNT - 1) / UNT;
   const long long target = 6LL * sm_count(c) * 3;
 
   for (int r0 = 0; r0 < N; r0 += nb) {
@@ -422,7 +468,9 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
       }
       sp.nosum = have_known ? 0 : 1;
       const int Wv = std::max(4, round4((top - h + 31) / 32));
-      const int Cs = colsum_width(W, Wv);
+      Sched sc;
+      CK(sched_for(c, W, Wv, 0, &sc));
+      const int Cs = sc.C;
       int rc = ensure_vec(c, Wv, Cs, nbs);
       if (rc) return rc;
       sp.vecA = c->vecA;
@@ -439,28 +487,23 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
                             c->stream));
         c->launches++;
       }
-      Unit *units = nullptr;
-      int nunits = 0;
-      CK(units_for(c, W, Wv, &units, &nunits));
       UpdParams up;
       std::memset(&up, 0, sizeof(up));
       up.mode = back ? M_GEMV_BACK : M_GEMV_FWD;
       up.N = N;
       up.A = c->A;
       up.Asign = c->Asign;
-      up.W = W;
+      up.astride = W;
       up.Vy = c->vecA;
       up.Vysign = c->vecAsign;
-      up.Wv = Wv;
-      up.Wx = W;
-      up.Wy = Wv;
+      up.vstride = Wv;
+      up.cx = W;
+      up.cy = Wv;
       up.r0 = B0;
       up.colsum = c->colsum_s;
-      up.C = Cs;
-      up.units = units;
-      up.nunits = nunits;
+      fill_sched(up, sc);
       up.st = c->st;
-      const long long cta_per_out = (nunits + UNT - 1) / UNT;
+      const long long cta_per_out = (sc.n + UNT - 1) / UNT;
       const long long target = 6LL * sm_count(c) * 3;
       if (have_known) {
         up.ra = B0;
@@ -520,16 +563,15 @@ int rayleigh(hk_ctx *c, int slot) {
   if (rc) return rc;
   if (lov == LLONG_MAX || low == LLONG_MAX) return HK_ERR_NOT_PD;
   const int Wd = std::max(4, round4(std::max((hiv - lov + 31) / 32, (hiw - low + 31) / 32)));
-  const int Cd = colsum_width(Wd, Wd);
+  Sched sc;
+  CK(sched_for(c, Wd, Wd, 0, &sc));
+  const int Cd = sc.C;
   rc = ensure_vec(c, Wd, Cd, 2);
   if (rc) return rc;
   ev_begin(c, 2);
   CK(launch_vec_align(0, N, c->v, L, nullptr, 0, lov, Wd, c->vecA, c->vecAsign, c->st, c->stream));
   CK(launch_vec_align(0, N, c->w, L, nullptr, 0, low, Wd, c->vecB, c->vecBsign, c->st, c->stream));
   CK(cudaMemsetAsync(c->colsum_s, 0, sizeof(long long) * 2 * Cd, c->stream));
-  Unit *units = nullptr;
-  int nunits = 0;
-  CK(units_for(c, Wd, Wd, &units, &nunits));
   UpdParams up;
   std::memset(&up, 0, sizeof(up));
   up.mode = M_DOT;
@@ -538,18 +580,15 @@ int rayleigh(hk_ctx *c, int slot) {
   up.Vxsign = c->vecAsign;
   up.Vy = c->vecB;
   up.Vysign = c->vecBsign;
-  up.Wv = Wd;
-  up.Wx = Wd;
-  up.Wy = Wd;
+  up.vstride = Wd;
+  up.cx = up.cy = Wd;
   up.nout = 2;
   up.t0 = 0;
   up.t1 = N;
   up.colsum = c->colsum_s;
-  up.C = Cd;
-  up.units = units;
-  up.nunits = nunits;
+  fill_sched(up, sc);
   up.st = c->st;
-  const long long cta_per_out = (nunits + UNT - 1) / UNT;
+  const long long cta_per_out = (sc.n + UNT - 1) / UNT;
   up.tchunk = pick_tchunk(N, cta_per_out * 2, 6LL * sm_count(c) * 3);
   CK(launch_update(up, c->stream));
   CK(launch_lambda(L, c->colsum_s, Cd, lov, low, c->hist, slot, c->st, c->stream));
@@ -654,22 +693,25 @@ void hk_destroy(hk_ctx *c) {
 }
 
 int hk_workspace_bytes(int N, int P, size_t *bytes) {
-  if (N < 1 || P < 32 || P % 32 || !bytes) return HK_ERR_ARG;
+  if (N < 1 || P < 32 || P % 32 || P > HK_MAX_P || !bytes) return HK_ERR_ARG;
   const long long L = P / 32;
   const long long W = round4(L + (N + 128 + 31) / 32) + 64;  // one widening included
   const long long NT = (long long)N * (N + 1) / 2;
-  const long long C = colsum_width((int)W, (int)W);
+  KarLayout kl;
+  kar_layout((int)W, 2, KAR_GAP, &kl);
+  const long long C = 2 * W + 64;
   long long b = 0;
   b += (2LL * N) * (16 + 4 * L);          // moments
   b += 3LL * N * 8 + 4096;                // tops, grids, status
   b += NT * (16 + 4 * L);                 // R
   b += NT * (4 * W + 4);                  // aligned R
+  b += NT * 4LL * kl.stride;              // its Karatsuba expansion
   b += (long long)N * (L + 2) * 4;        // reciprocals
   b += 16LL * N * C * 8;                  // column sums of one block
   b += 3LL * N * (16 + 4 * L) + 256LL * (16 + 4 * L);  // v, y, w, history
   const long long Wv = 2 * W + (long long)N;  // vector window (generous)
-  b += 2LL * N * (4 * Wv + 4) * 5 / 4 + 16LL * colsum_width((int)W, (int)Wv) * 8 * 5 / 4;
-  b += 1LL << 20;                         // unit tables, alignment slack
+  b += 2LL * N * (4 * Wv + 4) * 5 / 4 + 16LL * (W + Wv + 64) * 8 * 5 / 4;
+  b += 8LL << 20;                         // unit tables, alignment slack
   *bytes = (size_t)b * 2;                 // two widenings of slack for the bump allocator
   return HK_OK;
 }
@@ -691,7 +733,7 @@ int hk_set_workspace(hk_ctx *c, void *dev_ptr, size_t bytes) {
   c->colsum_s_cap = 0;
   c->fac_N = c->fac_L = c->fac_W = 0;
   c->mom = MpArr{};
-  c->unit_cache.clear();
+  c->sched_cache.clear();
   return HK_OK;
 }
 
@@ -727,7 +769,7 @@ int hk_load_moments_flat(hk_ctx *c, int N, int bnum, int bden, int P, const int3
       c->base_arena.cap = c->ws_bytes;
       c->base_arena.used = 0;
     }
-    c->unit_cache.clear();
+    c->sched_cache.clear();
     c->sol_ready = false;
     c->hist_cap = 0;
     c->vec_cap = 0;
@@ -777,6 +819,8 @@ int hk_factor(hk_ctx *c, int *bad_row) {
   c->t_phase[0] = c->t_phase[1] = c->t_phase[2] = 0;
   c->W = round4(c->L + (c->N + 128 + 31) / 32);
   c->top_margin = 0;
+  if (const char *e = getenv("HK_NB")) c->nb = std::max(1, atoi(e));  // panel block rows (tuning)
+  if (const char *e = getenv("HK_KARATSUBA")) c->kar_levels = std::min(2, std::max(0, atoi(e)));  // (tuning)
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);

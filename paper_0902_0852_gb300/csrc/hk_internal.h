@@ -8,30 +8,62 @@ namespace hk {
 
 // ---- exact contraction (hk_update.cu) ----------------------------------------
 // Stripe width (columns per thread) and p-steps per work unit.
-constexpr int UC = 9;
-constexpr int UPC = 36;
-constexpr int UNT = 256;      // compute threads per CTA
-constexpr int USTAGES = 4;    // shared-memory pipeline depth
+constexpr int UC = 9;          // default stripe width (result columns per thread)
+constexpr int UC_MAX = 13;
+constexpr int UPC = 36;        // default p-steps per unit (a multiple of the stripe width)
+constexpr int UNT = 256;       // compute threads per CTA
+constexpr int USTAGES = 4;     // shared-memory pipeline depth
+constexpr int MAX_SUB = 9;     // sub-contractions per launch (two Karatsuba levels)
+constexpr int MAX_TERMS = 4;   // result positions a sub-contraction is added to
 
 struct Unit {
-  int d0;  // first column of the stripe
+  int d0;  // first column of the stripe, sub-contraction index in bits 24..31
   int p0;  // first p (limb index of the X operand)
 };
 
 enum UpdMode { M_FACTOR = 0, M_GEMV_FWD = 1, M_GEMV_BACK = 2, M_DOT = 3 };
 
+// One integer contraction sum_t X_t[xoff..xoff+wx) * Y_t[yoff..yoff+wy), added
+// to the output's column sums at each (column offset, sign) term.
+struct SubProb {
+  int xoff, yoff;          // limb offset of the operand pieces inside an entry
+  int wx, wy;              // widths of the pieces in limbs
+  int nterm;
+  int toff[MAX_TERMS];
+  int tsign[MAX_TERMS];
+};
+
+// Karatsuba expansion of an aligned entry of W limbs (levels 0, 1 or 2):
+// pieces lo, hi, lo+hi (recursively), each stored in its own slot with zero
+// gaps of G limbs on both sides, so that one entry is one contiguous copy.
+struct KarLayout {
+  int levels;
+  int W;
+  int npieces;
+  int m1;                  // level-1 split
+  int m2[3];               // level-2 splits of lo, hi, lo+hi
+  int off[MAX_SUB];        // slot offsets (limbs)
+  int w[MAX_SUB];          // piece widths
+  int G;                   // gap (limbs)
+  int stride;              // expanded entry size (limbs)
+};
+
 struct UpdParams {
   int mode;
   int N;
-  const uint32_t *A;       // aligned R entries, W limbs each (packed upper triangle)
+  const uint32_t *A;       // R entries (plain, or expanded), packed upper triangle
   const int32_t *Asign;
-  int W;
-  const uint32_t *Vx;      // aligned vectors, Wv limbs per entry
+  int astride;             // limbs per A entry
+  const uint32_t *Vx;      // aligned vectors
   const int32_t *Vxsign;
   const uint32_t *Vy;
   const int32_t *Vysign;
-  int Wv;
-  int Wx, Wy;              // operand widths of this launch
+  int vstride;             // limbs per vector entry
+  int cx, cy;              // limbs copied per X / Y entry
+  int uc;                  // stripe width of the unit table (7, 9, 11 or 13)
+  int upc;                 // p-steps per unit (a multiple of uc)
+  int nsub;
+  SubProb sub[MAX_SUB];
   int r0;                  // first row of the current block (output indexing)
   int ra, rb;              // output rows [ra, rb)
   int nout;                // number of outputs
@@ -44,14 +76,19 @@ struct UpdParams {
   DevStatus *st;
 };
 
-// Number of work units and the unit table for operand widths (Wx, Wy).
-int build_units(int Wx, int Wy, Unit *host_out, int cap);
-int colsum_width(int Wx, int Wy);
+// Host-side schedule helpers.
+void kar_layout(int W, int levels, int gap, KarLayout *kl);
+int kar_subprobs(const KarLayout &kl, SubProb *sub);   // returns the count
+int build_units(const SubProb *sub, int nsub, int uc, int upc, Unit *host_out, int cap);
+void choose_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc, int *upc);
+int colsum_width(const SubProb *sub, int nsub, int uc);
 cudaError_t launch_update(const UpdParams &p, cudaStream_t s);
 
 // ---- panel kernels (hk_panel.cu) ------------------------------------------------
 struct PanelParams {
   int N, L, W, C;
+  KarLayout kl;            // expansion written next to each aligned entry (levels > 0)
+  uint32_t *Aexp;
   MpArr mom;               // moments (2N-1)
   const long long *colU;   // column top bounds U_j  (grid g_j = U_j - 32 W)
   MpArr R;                 // R in floating form (packed)

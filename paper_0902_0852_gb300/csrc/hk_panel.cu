@@ -136,6 +136,42 @@ HK_DEV bool align_entry(const uint32_t *mant, int L, long long e, bool zero, lon
   return true;
 }
 
+// Karatsuba expansion of the aligned entry a[0..W) (global, just written by
+// this block): pieces lo, hi and lo+hi of the split at m1, and for two levels
+// the same split of each of those, written into their slots of dst (zero gaps).
+template <int NT>
+HK_DEV void expand_entry(const uint32_t *a, const KarLayout &kl, uint32_t *dst, long long *cs, uint32_t *t1,
+                         uint32_t *t2, mp::Red &r) {
+  for (int l = threadIdx.x; l < kl.stride; l += NT) dst[l] = 0;
+  __syncthreads();
+  const int W = kl.W, m1 = kl.m1;
+  const int l1[3] = {m1, W - m1, max(m1, W - m1) + 1};
+  // level-1 sum lo + hi into t1
+  for (int l = threadIdx.x; l < l1[2]; l += NT)
+    cs[l] = (long long)mp::limb_at(a, m1, l) + (long long)mp::limb_at(a + m1, W - m1, l);
+  __syncthreads();
+  mp::normalize<NT>(cs, l1[2], t1, r);
+  if (kl.levels == 1) {
+    for (int l = threadIdx.x; l < l1[0]; l += NT) dst[kl.off[0] + l] = a[l];
+    for (int l = threadIdx.x; l < l1[1]; l += NT) dst[kl.off[1] + l] = a[m1 + l];
+    for (int l = threadIdx.x; l < l1[2]; l += NT) dst[kl.off[2] + l] = t1[l];
+    return;
+  }
+  for (int u = 0; u < 3; u++) {
+    const uint32_t *src = u == 0 ? a : (u == 1 ? a + m1 : t1);
+    const int wu = l1[u], m2 = kl.m2[u];
+    for (int l = threadIdx.x; l < m2; l += NT) dst[kl.off[3 * u] + l] = src[l];
+    for (int l = threadIdx.x; l < wu - m2; l += NT) dst[kl.off[3 * u + 1] + l] = src[m2 + l];
+    const int ws = kl.w[3 * u + 2];
+    for (int l = threadIdx.x; l < ws; l += NT)
+      cs[l] = (long long)mp::limb_at(src, m2, l) + (long long)mp::limb_at(src + m2, wu - m2, l);
+    __syncthreads();
+    mp::normalize<NT>(cs, ws, t2, r);
+    for (int l = threadIdx.x; l < ws; l += NT) dst[kl.off[3 * u + 2] + l] = t2[l];
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(NT_DIAG) k_diag(PanelParams p, int i) {
   if (p.st->code != ST_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -176,6 +212,9 @@ __global__ void __launch_bounds__(NT_DIAG) k_diag(PanelParams p, int i) {
   }
   align_entry<NT_DIAG>(s.rm, L, Rr.exp, false, gi, p.W, p.A + idx * p.W, p.st);
   __syncthreads();
+  if (p.kl.levels > 0)
+    expand_entry<NT_DIAG>(p.A + idx * p.W, p.kl, p.Aexp + idx * p.kl.stride, s.cs, s.Z, s.big, *s.red);
+  __syncthreads();
   ok = mp::recip<NT_DIAG>(s.rm, L, s.V, w, B);
   for (int l = threadIdx.x; l < L + 2; l += NT_DIAG) p.recip[(long long)i * (L + 2) + l] = s.V[l];
   if (threadIdx.x == 0 && !ok) atomicAdd(&p.st->timeout, 1);
@@ -206,6 +245,8 @@ __global__ void __launch_bounds__(NT_ROW) k_offdiag(PanelParams p, int i) {
   if (!S.nonzero) {
     for (int l = threadIdx.x; l < L; l += NT_ROW) p.R.limbs[idx * L + l] = 0;
     for (int l = threadIdx.x; l < p.W; l += NT_ROW) p.A[idx * p.W + l] = 0;
+    if (p.kl.levels > 0)
+      for (int l = threadIdx.x; l < p.kl.stride; l += NT_ROW) p.Aexp[idx * p.kl.stride + l] = 0;
     if (threadIdx.x == 0) {
       p.R.sign[idx] = 0;
       p.R.exp[idx] = 0;
@@ -225,7 +266,10 @@ __global__ void __launch_bounds__(NT_ROW) k_offdiag(PanelParams p, int i) {
     p.Asign[idx] = sgn < 0 ? 1 : 0;
     if (!ok) atomicAdd(&p.st->timeout, 1);
   }
-  align_entry<NT_ROW>(s.res, L, Q.exp, false, gj, p.W, p.A + idx * p.W, p.st);
+  if (align_entry<NT_ROW>(s.res, L, Q.exp, false, gj, p.W, p.A + idx * p.W, p.st) && p.kl.levels > 0) {
+    __syncthreads();
+    expand_entry<NT_ROW>(p.A + idx * p.W, p.kl, p.Aexp + idx * p.kl.stride, s.cs, s.Z, s.big, *s.red);
+  }
 }
 
 }  // namespace

@@ -1,39 +1,48 @@
 // The exact trailing-update contraction (the hot loop).
 //
 // For every output o it adds  sum_t sign_t * X_o(t) * Y_o(t)  exactly into 64-bit
-// column sums colsum[o][*], where X_o(t), Y_o(t) are non-negative integers of
-// Wx and Wy 32-bit limbs.  In the factorisation X_o(t) = a_ti and Y_o(t) = a_tj
-// are entries of R written on the common binary grid of their column, so
-// sum_{t<i} R_ti R_tj (the update of section "The LDL^T Determinant
-// Algorithm", M[row][col] -= C[col] * CDivDiag[row], applied for all earlier
-// columns at once) becomes this plain integer contraction; the same kernel
-// computes the blocked triangular-solve products and the dot products of
-// inverse iteration.
+// column sums colsum[o][*], where X_o(t), Y_o(t) are non-negative integers.  In the
+// factorisation X_o(t) = a_ti and Y_o(t) = a_tj are entries of R written on the
+// common binary grid of their column, so sum_{t<i} R_ti R_tj (the update of
+// section "The LDL^T Determinant Algorithm", M[row][col] -= C[col] * CDivDiag[row],
+// applied for all earlier columns at once) becomes this plain integer
+// contraction; the same kernel computes the blocked triangular-solve products
+// and the dot products of inverse iteration.
 //
-// Layout of the work: the Wx x Wy grid of limb products (p, q) of one output is
-// cut into stripes of UC consecutive result columns d = p + q, and each stripe's
-// p-range into chunks of UPC: one (stripe, chunk) "unit" per thread.  A thread
-// keeps a 96-bit accumulator (three words, mad.lo.cc / madc.hi.cc / addc) per
-// column of its stripe across all t of its chunk of the contraction, reading
-// X[p] and a sliding window of Y held in registers (one new Y limb per p).
-// Shared-memory operand rows are zero-padded so that products outside the
-// valid triangle vanish.  Entries are streamed into a USTAGES-deep ring by a
-// producer warp with 1-D TMA bulk copies (cp.async.bulk + mbarrier);
-// the eight compute warps release each stage with an mbarrier arrival.  All
-// waits are bounded: a wait that runs out records HK_ERR_TIMEOUT and the block
-// returns after waiting (again bounded) for its own copies in flight.
+// Karatsuba on the whole dot product: with a = a0 + a1 B,
+//   sum a_i a_j = C0 + B (Cs - C0 - C1) + B^2 C1,
+//   C0 = sum a0_i a0_j, C1 = sum a1_i a1_j, Cs = sum (a0+a1)_i (a0+a1)_j,
+// so one launch runs a list of smaller contractions ("sub-problems", up to
+// nine for two levels), each added to the column sums at (offset, sign) terms.
+// The identity is exact, so results do not depend on the expansion depth.
+//
+// Layout of the work: the wx x wy grid of limb products (p, q) of one
+// sub-problem is cut into stripes of UC consecutive result columns d = p + q,
+// and each stripe's p-range into chunks of `upc`: one (stripe, chunk) "unit"
+// per thread.  A thread keeps a 96-bit accumulator (three words,
+// mad.lo.cc / madc.hi.cc / addc) per column of its stripe across all t of its
+// chunk of the contraction, reading X[p] and a sliding window of Y held in
+// registers (one new Y limb per p).  Operand pieces are separated by zero gaps
+// so that products outside the valid triangle vanish.  Entries are streamed
+// into a USTAGES-deep ring by a producer warp with 1-D TMA bulk copies
+// (cp.async.bulk + mbarrier); the eight compute warps release each stage with
+// an mbarrier arrival.  All waits are bounded: a wait that runs out records
+// HK_ERR_TIMEOUT and the block returns after waiting (again bounded) for its
+// own copies in flight.
 #include "hk_internal.h"
 #include "hk_mp.cuh"
 #include <algorithm>
+#include <climits>
+#include <cstdlib>
 #include <vector>
 
 namespace hk {
 
 namespace {
 
-constexpr int XPADR = ((UPC + 3) / 4) * 4;
-constexpr int YPADL = ((UC + UPC + 3) / 4) * 4;
-constexpr int YPADR = ((UC + 3) / 4) * 4;
+__host__ __device__ inline int ypadr(int uc) { return ((uc + 3) / 4) * 4; }
+__host__ __device__ inline int xpadr(int upc) { return ((upc + 3) / 4) * 4; }
+__host__ __device__ inline int ypadl(int uc, int upc) { return ((uc + upc + 3) / 4) * 4; }
 constexpr long long SPIN_LIMIT = 1LL << 30;
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // 2 s
 
@@ -90,28 +99,28 @@ struct Operands {
   int neg;
 };
 
-// operand pointers of output (i, j) at contraction index t
+// operand entries of output (i, j) at contraction index t
 HK_DEV Operands operands(const UpdParams &p, int oi, int oj, int t) {
   Operands r;
   const long long N = p.N;
   if (p.mode == M_FACTOR) {
     const long long ia = tri_idx(t, oi, N), ja = tri_idx(t, oj, N);
-    r.x = p.A + ia * p.W;
-    r.y = p.A + ja * p.W;
+    r.x = p.A + ia * p.astride;
+    r.y = p.A + ja * p.astride;
     r.neg = p.Asign[ia] ^ p.Asign[ja];
   } else if (p.mode == M_GEMV_FWD) {
     const long long ia = tri_idx(t, oi, N);
-    r.x = p.A + ia * p.W;
-    r.y = p.Vy + (long long)t * p.Wv;
+    r.x = p.A + ia * p.astride;
+    r.y = p.Vy + (long long)t * p.vstride;
     r.neg = p.Asign[ia] ^ p.Vysign[t];
   } else if (p.mode == M_GEMV_BACK) {
     const long long ia = tri_idx(oi, t, N);
-    r.x = p.A + ia * p.W;
-    r.y = p.Vy + (long long)t * p.Wv;
+    r.x = p.A + ia * p.astride;
+    r.y = p.Vy + (long long)t * p.vstride;
     r.neg = p.Asign[ia] ^ p.Vysign[t];
   } else {  // M_DOT: output 0 = <x,x>, output 1 = <x,y>
-    r.x = p.Vx + (long long)t * p.Wv;
-    r.y = (oj == 0 ? p.Vx : p.Vy) + (long long)t * p.Wv;
+    r.x = p.Vx + (long long)t * p.vstride;
+    r.y = (oj == 0 ? p.Vx : p.Vy) + (long long)t * p.vstride;
     r.neg = p.Vxsign[t] ^ (oj == 0 ? p.Vxsign[t] : p.Vysign[t]);
   }
   return r;
@@ -141,14 +150,20 @@ HK_DEV void decode_output(const UpdParams &p, int o, int *oi, int *oj, long long
   }
 }
 
-__global__ void __launch_bounds__(UNT + 32) k_update(UpdParams p) {
+#ifndef HK_UPDATE_MINBLOCKS
+#define HK_UPDATE_MINBLOCKS 2
+#endif
+template <int UC>
+__global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const __grid_constant__ UpdParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int Xsz = ((p.Wx + XPADR + 3) / 4) * 4;
-  const int Ysz = ((YPADL + p.Wy + YPADR + 3) / 4) * 4;
+  const int XPADR = xpadr(p.upc), YPADL = ypadl(UC, p.upc), YPADR = ypadr(UC);
+  const int Xsz = ((p.cx + XPADR + 3) / 4) * 4;
+  const int Ysz = ((YPADL + p.cy + YPADR + 3) / 4) * 4;
   uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)USTAGES * (Xsz + Ysz) * 4);
   uint64_t *empty = full + USTAGES;
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + USTAGES);
+  int *sneg = reinterpret_cast<int *>(empty + USTAGES);  // sign of the stage's product
+  volatile int *abort_flag = sneg + USTAGES;
 
   if (p.st->code != ST_OK) return;  // an earlier step failed: nothing to do
 
@@ -158,13 +173,20 @@ __global__ void __launch_bounds__(UNT + 32) k_update(UpdParams p) {
   decode_output(p, o, &oi, &oj, &crow);
   int tb = p.t0 + blockIdx.z * p.tchunk;
   int te = min(p.t1, tb + p.tchunk);
-  if (p.mode == M_GEMV_FWD) te = min(te, oi);            // t < i
-  if (p.mode == M_GEMV_BACK) tb = max(tb, oi + 1);       // t > i
+  if (p.mode == M_GEMV_FWD) te = min(te, oi);       // t < i
+  if (p.mode == M_GEMV_BACK) tb = max(tb, oi + 1);  // t > i
   const int nt = te - tb;
   if (nt <= 0) return;
 
-  // zero the whole ring once (pads stay zero; TMA writes only the middle)
-  for (int k = threadIdx.x; k < USTAGES * (Xsz + Ysz); k += blockDim.x) bufs[k] = 0;
+  // zero the pads of the stages in use (TMA writes only the operand entries)
+  const int used = min(nt, USTAGES);
+  for (int s = 0; s < used; s++) {
+    uint32_t *xs = bufs + (size_t)s * (Xsz + Ysz);
+    for (int k = threadIdx.x; k < Xsz - p.cx; k += blockDim.x) xs[p.cx + k] = 0;
+    uint32_t *ys = xs + Xsz;
+    for (int k = threadIdx.x; k < YPADL; k += blockDim.x) ys[k] = 0;
+    for (int k = threadIdx.x; k < Ysz - YPADL - p.cy; k += blockDim.x) ys[YPADL + p.cy + k] = 0;
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < USTAGES; s++) {
       mbar_init(&full[s], 1);
@@ -177,7 +199,7 @@ __global__ void __launch_bounds__(UNT + 32) k_update(UpdParams p) {
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t bytesX = (uint32_t)p.Wx * 4u, bytesY = (uint32_t)p.Wy * 4u;
+  const uint32_t bytesX = (uint32_t)p.cx * 4u, bytesY = (uint32_t)p.cy * 4u;
 
   if (warp == UNT / 32) {
     // ---------------- producer warp ----------------
@@ -196,6 +218,7 @@ __global__ void __launch_bounds__(UNT + 32) k_update(UpdParams p) {
         const Operands op = operands(p, oi, oj, tb + it);
         uint32_t *xs = bufs + (size_t)s * (Xsz + Ysz);
         uint32_t *ys = xs + Xsz + YPADL;
+        sneg[s] = op.neg;
         mbar_expect_tx(&full[s], bytesX + bytesY);
         bulk_g2s(xs, op.x, bytesX, &full[s]);
         bulk_g2s(ys, op.y, bytesY, &full[s]);
@@ -213,7 +236,10 @@ __global__ void __launch_bounds__(UNT + 32) k_update(UpdParams p) {
   // ---------------- compute warps ----------------
   const int u = blockIdx.x * UNT + threadIdx.x;
   const bool active = u < p.nunits;
-  Unit un = active ? p.units[u] : Unit{0, 0};
+  const Unit un = active ? p.units[u] : Unit{0, 0};
+  const int sp = (un.d0 >> 24) & 0xff;
+  const int d0 = un.d0 & 0xffffff, p0 = un.p0;
+  const int xoff = p.sub[sp].xoff, yoff = p.sub[sp].yoff;
   uint32_t c0[UC], c1[UC], c2[UC];
 #pragma unroll
   for (int m = 0; m < UC; m++) c0[m] = c1[m] = c2[m] = 0;
@@ -226,17 +252,16 @@ __global__ void __launch_bounds__(UNT + 32) k_update(UpdParams p) {
       break;
     }
     if (*abort_flag) break;
-    const uint32_t *X = bufs + (size_t)s * (Xsz + Ysz);
-    const uint32_t *Y = X + Xsz + YPADL;
-    const Operands op = operands(p, oi, oj, tb + it);  // sign only
+    const uint32_t *X = bufs + (size_t)s * (Xsz + Ysz) + xoff;
+    const uint32_t *Y = bufs + (size_t)s * (Xsz + Ysz) + Xsz + YPADL + yoff;
+    const int neg = sneg[s];
     if (active) {
-      const int d0 = un.d0, p0 = un.p0;
       uint32_t wb[UC];
 #pragma unroll
       for (int m = 1; m < UC; m++) wb[m] = Y[d0 + m - p0];
-      if (!op.neg) {
+      if (!neg) {
 #pragma unroll 1
-        for (int b = 0; b < UPC / UC; b++) {
+        for (int b = 0; b < p.upc / UC; b++) {
 #pragma unroll
           for (int j = 0; j < UC; j++) {
             const int pp = p0 + b * UC + j;
@@ -248,7 +273,7 @@ __global__ void __launch_bounds__(UNT + 32) k_update(UpdParams p) {
         }
       } else {
 #pragma unroll 1
-        for (int b = 0; b < UPC / UC; b++) {
+        for (int b = 0; b < p.upc / UC; b++) {
 #pragma unroll
           for (int j = 0; j < UC; j++) {
             const int pp = p0 + b * UC + j;
@@ -266,66 +291,233 @@ __global__ void __launch_bounds__(UNT + 32) k_update(UpdParams p) {
 
   if (!active || *abort_flag) return;
   // flush: stripe words -> signed 64-bit column partial sums, added atomically
-  unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.colsum + crow * p.C + un.d0);
-  const int lim = p.C - un.d0;
+  // at every (offset, sign) term of the sub-problem
+  long long v[UC + 2];
 #pragma unroll
   for (int m = 0; m < UC + 2; m++) {
-    long long v = 0;
-    if (m < UC) v += (long long)c0[m];
-    if (m >= 1 && m <= UC) v += (long long)c1[m - 1];
-    if (m >= 2) v += (long long)(int32_t)c2[m - 2];
-    if (v != 0 && m < lim) atomicAdd(dst + m, (unsigned long long)v);
+    long long x = 0;
+    if (m < UC) x += (long long)c0[m];
+    if (m >= 1 && m <= UC) x += (long long)c1[m - 1];
+    if (m >= 2) x += (long long)(int32_t)c2[m - 2];
+    v[m] = x;
+  }
+  const int nterm = p.sub[sp].nterm;
+  for (int k = 0; k < nterm; k++) {
+    const int base = d0 + p.sub[sp].toff[k];
+    const long long sg = p.sub[sp].tsign[k];
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.colsum + crow * p.C + base);
+    const int lim = p.C - base;
+#pragma unroll
+    for (int m = 0; m < UC + 2; m++)
+      if (v[m] != 0 && m < lim) atomicAdd(dst + m, (unsigned long long)(sg * v[m]));
   }
 }
 
 }  // namespace
 
-int colsum_width(int Wx, int Wy) {
-  const int S = (Wx + Wy - 1 + UC - 1) / UC;
-  const int c = std::max(Wx + Wy + 2, S * UC + 2);
+// ---------------------------------------------------------------------------
+// host-side schedule helpers
+// ---------------------------------------------------------------------------
+
+void kar_layout(int W, int levels, int gap, KarLayout *kl) {
+  KarLayout k{};
+  k.levels = levels;
+  k.W = W;
+  k.G = ((gap + 3) / 4) * 4;
+  int w[MAX_SUB];
+  int n = 0;
+  if (levels <= 0) {
+    w[n++] = W;
+  } else {
+    k.m1 = (W + 1) / 2;
+    const int l1[3] = {k.m1, W - k.m1, std::max(k.m1, W - k.m1) + 1};
+    if (levels == 1) {
+      for (int u = 0; u < 3; u++) w[n++] = l1[u];
+    } else {
+      for (int u = 0; u < 3; u++) {
+        const int m2 = (l1[u] + 1) / 2;
+        k.m2[u] = m2;
+        w[n++] = m2;
+        w[n++] = l1[u] - m2;
+        w[n++] = std::max(m2, l1[u] - m2) + 1;
+      }
+    }
+  }
+  k.npieces = n;
+  int off = k.G;
+  for (int i = 0; i < n; i++) {
+    k.w[i] = w[i];
+    k.off[i] = off;
+    off += ((w[i] + 3) / 4) * 4 + k.G;
+  }
+  k.stride = ((off + 3) / 4) * 4;
+  *kl = k;
+}
+
+// Coefficients of the Karatsuba combination: the contraction of the lo, hi or
+// lo+hi pieces of a split at m is added at these offsets (limbs) and signs.
+static int coef(int which, int m, int *off, int *sg) {
+  if (which == 0) {  // lo*lo: +1 at 0, -1 at m
+    off[0] = 0;
+    sg[0] = 1;
+    off[1] = m;
+    sg[1] = -1;
+    return 2;
+  }
+  if (which == 1) {  // hi*hi: +1 at 2m, -1 at m
+    off[0] = 2 * m;
+    sg[0] = 1;
+    off[1] = m;
+    sg[1] = -1;
+    return 2;
+  }
+  off[0] = m;  // sum*sum: +1 at m
+  sg[0] = 1;
+  return 1;
+}
+
+int kar_subprobs(const KarLayout &kl, SubProb *sub) {
+  if (kl.levels <= 0) {
+    SubProb s{};
+    s.xoff = s.yoff = 0;
+    s.wx = s.wy = kl.W;
+    s.nterm = 1;
+    s.toff[0] = 0;
+    s.tsign[0] = 1;
+    sub[0] = s;
+    return 1;
+  }
+  for (int i = 0; i < kl.npieces; i++) {
+    SubProb s{};
+    s.xoff = s.yoff = kl.off[i];
+    s.wx = s.wy = kl.w[i];
+    int o1[2], s1[2];
+    if (kl.levels == 1) {
+      const int n1 = coef(i, kl.m1, o1, s1);
+      for (int a = 0; a < n1; a++) {
+        s.toff[a] = o1[a];
+        s.tsign[a] = s1[a];
+      }
+      s.nterm = n1;
+    } else {
+      const int u = i / 3, v = i % 3;
+      int o2[2], s2[2];
+      const int n1 = coef(u, kl.m1, o1, s1);
+      const int n2 = coef(v, kl.m2[u], o2, s2);
+      int n = 0;
+      for (int a = 0; a < n1; a++)
+        for (int b = 0; b < n2; b++) {
+          s.toff[n] = o1[a] + o2[b];
+          s.tsign[n] = s1[a] * s2[b];
+          n++;
+        }
+      s.nterm = n;
+    }
+    sub[i] = s;
+  }
+  return kl.npieces;
+}
+
+// column sums needed: every stripe of every sub-problem, flushed two columns
+// past its end, at every term offset
+int colsum_width(const SubProb *sub, int nsub, int uc) {
+  int c = 0;
+  for (int k = 0; k < nsub; k++) {
+    const int S = (sub[k].wx + sub[k].wy - 1 + uc - 1) / uc;
+    for (int t = 0; t < sub[k].nterm; t++) c = std::max(c, sub[k].toff[t] + S * uc + 2);
+  }
   return ((c + 3) / 4) * 4;
 }
 
-// Units in chunk-major order: for chunk k, consecutive stripes, so that the
-// threads of a warp read X[p] at one address (or stride UC) and Y with stride UC
-// (UC odd: no shared-memory bank conflicts).
-int build_units(int Wx, int Wy, Unit *out, int cap) {
-  const int S = (Wx + Wy - 1 + UC - 1) / UC;
-  std::vector<int> plo(S), len(S);
-  int kmax = 0;
-  for (int s = 0; s < S; s++) {
-    const int d0 = s * UC;
-    const int lo = std::max(0, d0 - Wy + 1);
-    const int hi = std::min(Wx - 1, d0 + UC - 1);
-    plo[s] = lo;
-    len[s] = hi >= lo ? hi - lo + 1 : 0;
-    kmax = std::max(kmax, (len[s] + UPC - 1) / UPC);
-  }
+// Units in chunk-major order per sub-problem: for chunk k, consecutive
+// stripes, so that the threads of a warp read X[p] at one address (or stride
+// uc) and Y with stride uc (uc odd: no shared-memory bank conflicts).
+int build_units(const SubProb *sub, int nsub, int uc, int upc, Unit *out, int cap) {
   int n = 0;
-  for (int k = 0; k < kmax; k++)
-    for (int s = 0; s < S; s++)
-      if (k * UPC < len[s]) {
-        if (out && n < cap) out[n] = Unit{s * UC, plo[s] + k * UPC};
-        n++;
-      }
+  for (int q = 0; q < nsub; q++) {
+    const int Wx = sub[q].wx, Wy = sub[q].wy;
+    const int S = (Wx + Wy - 1 + uc - 1) / uc;
+    std::vector<int> plo(S), len(S);
+    int kmax = 0;
+    for (int s = 0; s < S; s++) {
+      const int d0 = s * uc;
+      const int lo = std::max(0, d0 - Wy + 1);
+      const int hi = std::min(Wx - 1, d0 + uc - 1);
+      plo[s] = lo;
+      len[s] = hi >= lo ? hi - lo + 1 : 0;
+      kmax = std::max(kmax, (len[s] + upc - 1) / upc);
+    }
+    for (int k = 0; k < kmax; k++)
+      for (int s = 0; s < S; s++)
+        if (k * upc < len[s]) {
+          if (out && n < cap) out[n] = Unit{(q << 24) | (s * uc), plo[s] + k * upc};
+          n++;
+        }
+  }
   return n;
 }
 
-cudaError_t launch_update(const UpdParams &p, cudaStream_t s) {
-  if (p.nout <= 0 || p.t1 <= p.t0 || p.nunits <= 0) return cudaSuccess;
-  const int Xsz = ((p.Wx + XPADR + 3) / 4) * 4;
-  const int Ysz = ((YPADL + p.Wy + YPADR + 3) / 4) * 4;
-  const size_t smem = (size_t)USTAGES * (Xsz + Ysz) * 4 + 2 * USTAGES * 8 + 16;
+// Schedule: stripe width and chunk length (a multiple of it, at most upc_cap)
+// with the fewest thread-products per t including idle threads of the last
+// block and a per-unit window reload; HK_UC / HK_UPC override (tuning runs).
+void choose_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc_out, int *upc_out) {
+  int uc_force = 0, upc_force = 0;
+  if (const char *e = getenv("HK_UC")) uc_force = atoi(e);
+  if (const char *e = getenv("HK_UPC")) upc_force = atoi(e);
+  // inner-loop limb products per clock per SM by stripe width (measured on GB300)
+  const int ucs[3] = {7, 9, 11};
+  const double speed[3] = {21.5, 22.7, 23.4};
+  int best_uc = UC, best_upc = 4 * UC;
+  double best = 1e300;
+  for (int ui = 0; ui < 3; ui++) {
+    const int uc = ucs[ui];
+    if (uc_force && uc != uc_force) continue;
+    for (int upc = 2 * uc; upc <= 8 * uc && upc <= upc_cap; upc += uc) {
+      if (upc_force && upc != upc_force) continue;
+      const int n = build_units(sub, nsub, uc, upc, nullptr, 0);
+      const int blocks = (n + UNT - 1) / UNT;
+      const double cost = ((double)blocks * UNT * upc * uc + (double)n * 12 * uc) / speed[ui];
+      if (cost < best) {
+        best = cost;
+        best_uc = uc;
+        best_upc = upc;
+      }
+    }
+  }
+  *uc_out = best_uc;
+  *upc_out = best_upc;
+}
+
+namespace {
+
+template <int UCT>
+cudaError_t launch_uc(const UpdParams &p, cudaStream_t s) {
+  const int Xsz = ((p.cx + xpadr(p.upc) + 3) / 4) * 4;
+  const int Ysz = ((ypadl(UCT, p.upc) + p.cy + ypadr(UCT) + 3) / 4) * 4;
+  const size_t smem = (size_t)USTAGES * (Xsz + Ysz) * 4 + 2 * USTAGES * 8 + 4 * (USTAGES + 4);
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_update<UCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
   const int nz = (p.t1 - p.t0 + p.tchunk - 1) / p.tchunk;
   dim3 grid((p.nunits + UNT - 1) / UNT, p.nout, nz);
-  k_update<<<grid, UNT + 32, smem, s>>>(p);
+  k_update<UCT><<<grid, UNT + 32, smem, s>>>(p);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_update(const UpdParams &p, cudaStream_t s) {
+  if (p.nout <= 0 || p.t1 <= p.t0 || p.nunits <= 0) return cudaSuccess;
+  if (p.upc % p.uc != 0 || p.nsub < 1 || p.nsub > MAX_SUB) return cudaErrorInvalidValue;
+  switch (p.uc) {
+    case 7: return launch_uc<7>(p, s);
+    case 9: return launch_uc<9>(p, s);
+    case 11: return launch_uc<11>(p, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace hk
