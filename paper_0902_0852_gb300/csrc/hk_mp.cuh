@@ -200,25 +200,35 @@ struct Work {
   Red *r;
 };
 
-// out[0..nx+ny+2) = x[0..nx) * y[0..ny)   (x, y >= 0).  One thread per output
-// column sums its limb products exactly in three words, then adds the words
-// into the 64-bit column sums of columns d, d+1, d+2 (shared-memory atomics);
-// the top column holds a single product, so column nx+ny stays zero.
+// Column sums of the product x * y restricted to columns [dlo, dhi): column d
+// holds sum_{p+q=d} x_p y_q.  One thread per output column sums its limb
+// products exactly in three words, then adds the words into the 64-bit column
+// sums of columns d, d+1, d+2 (shared-memory atomics).  cs[k] is the sum of
+// column dlo + k; cs has dhi - dlo + 2 entries.
 template <int NT>
-HK_DEV void mul(const uint32_t *x, int nx, const uint32_t *y, int ny, uint32_t *out, Work &w) {
-  const int nc = nx + ny;
-  for (int d = threadIdx.x; d < nc + 2; d += NT) w.cs[d] = 0;
+HK_DEV void mul_cols(const uint32_t *x, int nx, const uint32_t *y, int ny, int dlo, int dhi, Work &w) {
+  const int n = dhi - dlo;
+  for (int d = threadIdx.x; d < n + 2; d += NT) w.cs[d] = 0;
   __syncthreads();
   unsigned long long *cu = reinterpret_cast<unsigned long long *>(w.cs);
-  for (int d = threadIdx.x; d < nc; d += NT) {
+  for (int k = threadIdx.x; k < n; k += NT) {
+    const int d = dlo + k;
     uint32_t c0 = 0, c1 = 0, c2 = 0;
     const int plo = max(0, d - ny + 1), phi = min(nx - 1, d);
     for (int p = plo; p <= phi; p++) mac3(c0, c1, c2, x[p], y[d - p]);
-    if (c0) atomicAdd(cu + d, (unsigned long long)c0);
-    if (c1) atomicAdd(cu + d + 1, (unsigned long long)c1);
-    if (c2) atomicAdd(cu + d + 2, (unsigned long long)c2);
+    if (c0) atomicAdd(cu + k, (unsigned long long)c0);
+    if (c1) atomicAdd(cu + k + 1, (unsigned long long)c1);
+    if (c2) atomicAdd(cu + k + 2, (unsigned long long)c2);
   }
   __syncthreads();
+}
+
+// out[0..nx+ny+2) = x[0..nx) * y[0..ny)   (x, y >= 0); the top column holds a
+// single product, so column nx+ny stays zero.
+template <int NT>
+HK_DEV void mul(const uint32_t *x, int nx, const uint32_t *y, int ny, uint32_t *out, Work &w) {
+  const int nc = nx + ny;
+  mul_cols<NT>(x, nx, y, ny, 0, nc, w);
   normalize<NT>(w.cs, nc, out, *w.r);
 }
 
@@ -570,56 +580,62 @@ HK_DEV Rounded sqrt_rne(const uint32_t *s, int L, long long e, uint32_t *mant, W
 }
 
 // mant, exponent of RNE_P(|num| 2^ne / (den 2^de)) where V = floor(2^(2P+1)/den).
-// num, den: normalised P-bit mantissas.  big: capacity >= 4L + 32.
+// num, den: normalised P-bit mantissas.  big: capacity >= 2L + 16.
+// Q = floor(num 2^(P+1) / den) (P+1 or P+2 bits) comes from the columns >= L-2
+// of num * V only: the dropped columns sum to less than (L-2) 2^(32(L-1)) <
+// 2^(32L), one unit of Q, and the Barrett estimate is at most one unit low, so
+// Q0 <= Q <= Q0 + 2.  The
+// remainder num 2^(P+1) - Q0 den lies in [0, 3 den) and is computed exactly
+// from the low L+3 limbs of Q0 * den; the correction then raises Q0 to Q.
 template <int NT>
 HK_DEV Rounded div_rne(const uint32_t *num, long long ne, const uint32_t *den, long long de,
                        const uint32_t *V, int L, uint32_t *mant, Work &w, uint32_t *big,
                        uint32_t *q, bool *ok) {
   const long long P = 32LL * L;
-  // Q0 = floor(num * V / 2^P)
-  mul<NT>(num, L, V, L + 2, big, w);
   const int nQ = L + 3;
-  shr<NT>(big, 2 * L + 4, P, q, nQ);
+  // high columns of num * V: value sum_{d >= L-2} col_d 2^(32 d)
+  const int dlo = max(0, L - 2), dhi = 2 * L + 2;
+  mul_cols<NT>(num, L, V, L + 2, dlo, dhi, w);
+  normalize<NT>(w.cs, dhi - dlo, big, *w.r);  // big = that sum / 2^(32 dlo)
+  // Q0 = floor(sum / 2^P)
+  shr<NT>(big, dhi - dlo + 2, 32LL * (L - dlo), q, nQ);
   __syncthreads();
+  // rem = num 2^(P+1) - Q0 den  mod 2^(32 nR), exact since 0 <= rem < 3 den
+  const int nR = L + 3;
+  mul_cols<NT>(q, nQ, den, L, 0, nR, w);
+  const long long pos = P + 1;
+  for (int d = threadIdx.x; d < nR; d += NT) {
+    const uint32_t a = limb_at(num, L, d - (int)(pos >> 5));
+    const uint32_t b = limb_at(num, L, d - (int)(pos >> 5) - 1);
+    const int bb = (int)(pos & 31);
+    const uint32_t sv = bb ? ((a << bb) | (b >> (32 - bb))) : a;
+    w.cs[d] = (long long)sv - w.cs[d];
+  }
+  __syncthreads();
+  // resolve modulo 2^(32 nR): the true value is non-negative and < 2^(32 nR)
+  normalize<NT>(w.cs, nR, big, *w.r);  // big[0..nR) = rem (limbs above nR are the wrap)
   bool done = false;
   bool sticky = true;
+  int adj = 0;
   for (int it = 0; it < 4 && !done; it++) {
-    // rem = num * 2^(P+1) - Q0 * den
-    mul<NT>(q, nQ, den, L, big, w);
-    const int nR = nQ + L + 2;
-    const long long pos = P + 1;
-    for (int d = threadIdx.x; d < nR; d += NT) {
-      const uint32_t a = limb_at(num, L, d - (int)(pos >> 5));
-      const uint32_t b = limb_at(num, L, d - (int)(pos >> 5) - 1);
-      const int bb = (int)(pos & 31);
-      const uint32_t sv = bb ? ((a << bb) | (b >> (32 - bb))) : a;
-      w.cs[d] = (long long)sv - (long long)big[d];
-    }
+    // rem >= den ?
+    for (int d = threadIdx.x; d < nR; d += NT) w.cs[d] = (long long)big[d] - (long long)limb_at(den, L, d);
     __syncthreads();
-    const bool rneg = resolve<NT>(w.cs, nR, big, *w.r);
-    // big now holds |rem|
-    int adj = 0;
-    if (rneg) {
-      adj = -1;
+    const bool neg = normalize<NT>(w.cs, nR, big + (nR + 4), *w.r);
+    // two's complement in nR+2 limbs: negative means rem < den
+    if (neg) {
+      sticky = bitlen<NT>(big, nR, *w.r) != 0;
+      done = true;
     } else {
-      const bool ge = !lincomb<NT>(big, nR + 2, 1, den, L, -1, nR + 2, big + (nR + 4), w);
-      if (ge) adj = 1;
-      else {
-        sticky = bitlen<NT>(big, nR + 2, *w.r) != 0;
-        done = true;
-      }
-    }
-    if (!done) {
-      for (int d = threadIdx.x; d < nQ; d += NT) w.cs[d] = (long long)q[d] + (d == 0 ? adj : 0);
+      copy<NT>(big + (nR + 4), nR, big, nR);
       __syncthreads();
-      normalize<NT>(w.cs, nQ, big, *w.r);
-      copy<NT>(big, nQ, q, nQ);
-      __syncthreads();
+      adj++;
     }
   }
   *ok = done;
+  // Q = Q0 + adj; result value (2Q + sticky) 2^(ne - de - P - 2)
   for (int d = threadIdx.x; d < nQ + 1; d += NT)
-    w.cs[d] = 2LL * limb_at(q, nQ, d) + ((d == 0 && sticky) ? 1 : 0);
+    w.cs[d] = 2LL * limb_at(q, nQ, d) + (d == 0 ? 2LL * adj + (sticky ? 1 : 0) : 0);
   __syncthreads();
   normalize<NT>(w.cs, nQ + 1, big, *w.r);
   return round_rne<NT>(big, nQ + 3, ne - de - P - 2, L, mant, w);

@@ -13,8 +13,8 @@ namespace hk {
 
 namespace {
 
-constexpr int NT_DIAG = 256;
-constexpr int NT_ROW = 128;
+constexpr int NT_DIAG = 512;
+constexpr int NT_ROW = 256;
 
 // a priori top bit bound of column j: |R_tj| <= sqrt(m_2j) < 2^U_j
 __global__ void k_col_tops(int N, int L, MpArr mom, long long *colU, long long top_margin) {

@@ -16,8 +16,8 @@ namespace hk {
 
 namespace {
 
-constexpr int NT_SOLVE = 128;
-constexpr int NT_LAM = 256;
+constexpr int NT_SOLVE = 512;
+constexpr int NT_LAM = 512;
 
 struct SSmem {
   mp::Red *red;
