@@ -120,3 +120,37 @@ def test_signed_entries(hk):
     assert R == Ro
     _, hist_o, _ = oracle.inverse_iteration(Ro, P, 6)
     assert hist == hist_o
+
+
+def _digest_flat(sign, exp, limbs):
+    """SHA-256 of R in the layout of tests/golden/make_golden.py: per entry,
+    sign (int32), exponent (int64), limbs (uint32), little endian, packed."""
+    import hashlib
+    import numpy as np
+    L = limbs.shape[1]
+    rec = np.zeros(len(sign), dtype=np.dtype([("s", "<i4"), ("e", "<i8"), ("l", "<u4", (L,))], align=False))
+    rec["s"] = sign
+    rec["e"] = exp
+    rec["l"] = limbs
+    return hashlib.sha256(rec.tobytes()).hexdigest()
+
+
+@pytest.mark.parametrize("name", ["config2_beta1", "config2_beta7_4"])
+def test_config2_against_stored_oracle(hk, name):
+    """N = 256, P = 8192, beta = 1 and 7/4 (moments rounded from Gamma values
+    with guard bits): R bit for bit (digest) and lambda_1..lambda_10 against
+    values the oracle wrote (tests/golden/make_golden.py)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name + ".json")
+    g = json.load(open(path))
+    N, P, T, beta = g["N"], g["P"], g["T"], tuple(g["beta"])
+    m = inputs.moments(N, beta, P)
+    with hk.Hankel(0) as h:
+        h.load(N, beta, P, m)
+        h.factor()
+        digest = _digest_flat(*hk.hk_get_R_flat(h.ctx, N, P))
+        lam, used = h.smallest_eig(T)
+        hist = h.history(T)
+    assert digest == g["R_sha256"]
+    assert hist == [(int(n), e) for n, e in g["history"]]
