@@ -288,6 +288,8 @@ def main():
     eig_ms = sum(r[2]["eig_ms"] for r in recs)
     limbprod = (N - 1) * N * (N + 1) // 6 * L * L * args.steps
     achieved = limbprod / (upd_ms / 1e3) / 1e12
+    st = recs[-1][3]
+    executed = (N - 1) * N * (N + 1) // 6 * st["limbprod_per_mac"] * args.steps / (upd_ms / 1e3) / 1e12
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     peak = n_sm * 64 * max_mhz * 1e6 / 2 / 1e12
@@ -318,7 +320,11 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_update (exact trailing update), factor launches",
                      "peak_basis": f"{n_sm} SMs x 64 IMAD/clk/SM x {max_mhz:.0f} MHz / 2 IMAD per 32x32->64 "
-                                   f"limb product (probe: {peaks['imad_per_clk_sm']:.1f} IMAD/clk/SM)"},
+                                   f"limb product (probe: {peaks['imad_per_clk_sm']:.1f} IMAD/clk/SM)",
+                     "achieved_basis": f"algorithmic L^2 = {L * L} limb products per MAC (schoolbook count); the "
+                                       f"kernel executes {st['limbprod_per_mac']} per MAC ({st['karatsuba_levels']} "
+                                       f"Karatsuba levels on window W = {st['W']})",
+                     "executed": executed, "executed_frac": executed / peak},
         "int_probe": peaks,
         "clocks": clocks,
         "gpu_launches": sum(r[3]["launches"] for r in recs),

@@ -132,7 +132,8 @@ int hk_get_timings(hk_ctx *ctx, double *out, int n);
 
 /* Launch statistics of the last hk_factor + hk_smallest_eig: out[0] kernels
  * launched, out[1] exact-accumulation window width W in limbs, out[2]
- * widenings taken. */
+ * widenings taken, out[3] Karatsuba levels of the factor update, out[4] limb
+ * products the update executes per P-bit multiply-accumulate. */
 int hk_get_stats(hk_ctx *ctx, int64_t *out, int n);
 
 /* ----- measurement hook ------------------------------------------------------

@@ -997,9 +997,17 @@ int hk_get_timings(hk_ctx *c, double *out, int n) {
 
 int hk_get_stats(hk_ctx *c, int64_t *out, int n) {
   if (!c || !out || n < 0) return HK_ERR_ARG;
-  const int64_t v[3] = {c->launches, c->W, c->widenings};
-  for (int k = 0; k < n && k < 3; k++) out[k] = v[k];
-  for (int k = 3; k < n; k++) out[k] = 0;
+  // limb products the factor's update kernel executes per P-bit MAC (sum of
+  // the sub-contraction areas; W^2 without Karatsuba)
+  SubProb sub[MAX_SUB];
+  KarLayout kl;
+  kar_layout(c->W, c->kar_levels, KAR_GAP, &kl);
+  const int ns = kar_subprobs(kl, sub);
+  int64_t per_mac = 0;
+  for (int k = 0; k < ns; k++) per_mac += (int64_t)sub[k].wx * sub[k].wy;
+  const int64_t v[5] = {c->launches, c->W, c->widenings, c->kar_levels, per_mac};
+  for (int k = 0; k < n && k < 5; k++) out[k] = v[k];
+  for (int k = 5; k < n; k++) out[k] = 0;
   return HK_OK;
 }
 

@@ -224,9 +224,10 @@ def hk_get_timings(ctx):
 
 
 def hk_get_stats(ctx):
-    out = (ctypes.c_int64 * 3)()
-    _check(lib().hk_get_stats(ctx, out, 3), "hk_get_stats")
-    return {"launches": out[0], "W": out[1], "widenings": out[2]}
+    out = (ctypes.c_int64 * 5)()
+    _check(lib().hk_get_stats(ctx, out, 5), "hk_get_stats")
+    return {"launches": out[0], "W": out[1], "widenings": out[2], "karatsuba_levels": out[3],
+            "limbprod_per_mac": out[4]}
 
 
 def hk_selftest_mp(op, L, x, ex=0, y=None, ey=0):

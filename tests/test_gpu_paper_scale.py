@@ -1,0 +1,52 @@
+"""Paper-scale check through the C ABI at the benchmark's launch configuration:
+N = 1000, beta = 1, P = 24576.  Every moment, R entry and partial sum is an
+integer below 2^P here, so the once-rounded factorisation is exact and R must
+equal the closed form R_ki = i! C(i, k) in all 500500 entries.  lambda_min after
+convergence is compared with Table 3 (1.0892e-52) and Table 1 (cond lower
+bound 7.62e5780 = Gamma(1999) / lambda_1)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_0902_0852_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_paper_scale_R_closed_form_and_lambda():
+    from paper_0902_0852_gb300 import build, hk
+    build.build()
+    N, P = 1000, 24576
+    L = P // 32
+    m = inputs.moments(N, (1, 1), P)
+    with hk.Hankel(0) as h:
+        h.load(N, (1, 1), P, m)
+        h.factor()
+        sign, exp, limbs = hk.hk_get_R_flat(h.ctx, N, P)
+        lam, used = h.smallest_eig(0)
+    assert not sign.any()
+    raw = np.ascontiguousarray(limbs).tobytes()
+    idx = 0
+    fact = 1
+    for t in range(N):
+        # row t: R_tj = j! C(j, t) for j >= t
+        fj = math.factorial(t)
+        c = 1  # C(j, t) at j = t
+        for j in range(t, N):
+            if j > t:
+                fj *= j
+                c = c * j // (j - t)
+            want = fj * c
+            n = int.from_bytes(raw[4 * L * idx: 4 * L * (idx + 1)], "little")
+            e = int(exp[idx])
+            got = n << e if e >= 0 else (n >> -e if n & ((1 << -e) - 1) == 0 else None)
+            assert got == want, (t, j)
+            idx += 1
+    n, e = lam
+    lg = math.log10(n) + e * math.log10(2)
+    ex = math.floor(lg)
+    assert round(10 ** (lg - ex), 4) == 1.0892 and ex == -52, (lg, used)
+    cond = math.lgamma(1999) / math.log(10) - lg
+    ce = math.floor(cond)
+    assert round(10 ** (cond - ce), 2) == 7.62 and ce == 5780
