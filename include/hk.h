@@ -106,6 +106,15 @@ int hk_load_moments_flat(hk_ctx *ctx, int N, int beta_num, int beta_den, int P,
  * first row whose rounded pivot is <= 0, as the oracle reports it. */
 int hk_factor(hk_ctx *ctx, int *bad_row);
 
+/* Select the kernel of the factorisation's trailing update for later
+ * hk_factor calls: path 0 (default) = exact product scanning on the integer
+ * multiply-add pipe with two Karatsuba levels; path 1 = the same exact
+ * contraction on the INT8 tensor path (mma.sync m16n8k32 u8 x u8 -> s32 over
+ * the bytes of the aligned entries, 64-bit drains).  Both give bit-identical R
+ * (the contraction is exact integer arithmetic either way).  Invalidates a
+ * previous factorisation. */
+int hk_set_update_path(hk_ctx *ctx, int path);
+
 /* Copy R (row-major packed upper triangle, N(N+1)/2 entries, entry (t, j),
  * j >= t, at index t*N - t*(t-1)/2 + (j - t)) to host hk_mp values whose
  * limbs arrays the caller provides. */

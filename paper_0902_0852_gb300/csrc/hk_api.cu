@@ -83,6 +83,7 @@ struct hk_ctx {
   uint32_t *Aexp = nullptr;  // Karatsuba expansion of A (levels > 0)
   KarLayout kl{};
   int kar_levels = 2;
+  int update_path = 0;       // 0: IMAD product scanning, 1: INT8 mma.sync
   int32_t *Asign = nullptr;
   uint32_t *recip = nullptr;
   long long *colsum = nullptr;
@@ -266,7 +267,7 @@ __global__ void k_col_grid(int N, const long long *colU, int W, long long *colG)
 int factor_attempt(hk_ctx *c) {
   const int N = c->N, L = c->L, W = c->W, nb = c->nb;
   const size_t NT = (size_t)N * (N + 1) / 2;
-  const int levels = c->kar_levels;
+  const int levels = c->update_path == 1 ? 0 : c->kar_levels;
   kar_layout(W, levels, KAR_GAP, &c->kl);
   Sched sc;
   CK(sched_for(c, W, W, levels, &sc));
@@ -339,7 +340,7 @@ int factor_attempt(hk_ctx *c) {
       up.t1 = r0;
       up.tchunk = pick_tchunk(r0, cta_per_out * nout, target);
       ev_begin(c, 0);
-      CK(launch_update(up, c->stream));
+      CK(c->update_path == 1 ? launch_update_i8(up, c->stream) : launch_update(up, c->stream));
       ev_end(c);
       c->launches++;
     }
@@ -357,7 +358,7 @@ int factor_attempt(hk_ctx *c) {
         up.t1 = i + 1;
         up.tchunk = 1;
         ev_begin(c, 0);
-        CK(launch_update(up, c->stream));
+        CK(c->update_path == 1 ? launch_update_i8(up, c->stream) : launch_update(up, c->stream));
         ev_end(c);
         c->launches++;
       }
@@ -868,6 +869,13 @@ int hk_factor(hk_ctx *c, int *bad_row) {
   return result;
 }
 
+int hk_set_update_path(hk_ctx *c, int path) {
+  if (!c || path < 0 || path > 1) return HK_ERR_ARG;
+  c->update_path = path;
+  c->factored = false;
+  return HK_OK;
+}
+
 int hk_get_R_flat(hk_ctx *c, int32_t *sign, int64_t *exp, uint32_t *limbs) {
   if (!c || !sign || !exp || !limbs) return HK_ERR_ARG;
   if (!c->factored) return HK_ERR_STATE;
@@ -1001,11 +1009,11 @@ int hk_get_stats(hk_ctx *c, int64_t *out, int n) {
   // the sub-contraction areas; W^2 without Karatsuba)
   SubProb sub[MAX_SUB];
   KarLayout kl;
-  kar_layout(c->W, c->kar_levels, KAR_GAP, &kl);
+  kar_layout(c->W, c->update_path == 1 ? 0 : c->kar_levels, KAR_GAP, &kl);
   const int ns = kar_subprobs(kl, sub);
   int64_t per_mac = 0;
   for (int k = 0; k < ns; k++) per_mac += (int64_t)sub[k].wx * sub[k].wy;
-  const int64_t v[5] = {c->launches, c->W, c->widenings, c->kar_levels, per_mac};
+  const int64_t v[5] = {c->launches, c->W, c->widenings, c->update_path == 1 ? 0 : c->kar_levels, per_mac};
   for (int k = 0; k < n && k < 5; k++) out[k] = v[k];
   for (int k = 5; k < n; k++) out[k] = 0;
   return HK_OK;

@@ -83,6 +83,9 @@ int build_units(const SubProb *sub, int nsub, int uc, int upc, Unit *host_out, i
 void choose_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc, int *upc);
 int colsum_width(const SubProb *sub, int nsub, int uc);
 cudaError_t launch_update(const UpdParams &p, cudaStream_t s);
+// INT8 tensor-core (mma.sync u8) form of the FACTOR update, plain entries
+cudaError_t launch_update_i8(const UpdParams &p, cudaStream_t s);
+size_t update_i8_smem(int W);
 
 // ---- panel kernels (hk_panel.cu) ------------------------------------------------
 struct PanelParams {

@@ -24,7 +24,7 @@ EXPORTS = [
     "hk_create", "hk_destroy", "hk_strerror", "hk_workspace_bytes", "hk_set_workspace",
     "hk_load_moments", "hk_load_moments_flat", "hk_factor", "hk_get_R", "hk_get_R_flat",
     "hk_smallest_eig", "hk_get_history_flat", "hk_get_timings", "hk_get_stats", "hk_selftest_mp",
-    "hk_probe_int_peaks", "hk_mp_op_noalloc",
+    "hk_probe_int_peaks", "hk_mp_op_noalloc", "hk_set_update_path",
 ]
 
 
@@ -68,6 +68,7 @@ def lib():
         L.hk_selftest_mp.argtypes = [i32, i32, PU32, i32, i64, PU32, i32, i64, PU32, P64]
         L.hk_probe_int_peaks.argtypes = [i32, ctypes.POINTER(ctypes.c_double), i32]
         L.hk_mp_op_noalloc.argtypes = [i32, i32, vp, i32, i64, vp, i32, i64, vp, vp, vp]
+        L.hk_set_update_path.argtypes = [vp, i32]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype if name in ("hk_destroy", "hk_strerror") else i32
         _lib = L
@@ -308,6 +309,10 @@ class Hankel:
 
     def factor(self):
         hk_factor(self.ctx)
+
+    def set_update_path(self, path):
+        """0: IMAD product scanning (default), 1: INT8 tensor instruction."""
+        _check(lib().hk_set_update_path(self.ctx, path), "hk_set_update_path")
 
     def R(self):
         return hk_get_R(self.ctx, self.N, self.P)

@@ -154,3 +154,36 @@ def test_config2_against_stored_oracle(hk, name):
         hist = h.history(T)
     assert digest == g["R_sha256"]
     assert hist == [(int(n), e) for n, e in g["history"]]
+
+
+@pytest.mark.parametrize("N,beta,P", [(40, (7, 4), 384), (64, (1, 1), 2048), (33, (3, 4), 512)])
+def test_int8_tensor_path_bit_identical(hk, N, beta, P):
+    """The INT8 tensor-core update (mma.sync u8, 64-bit drains) gives the same R,
+    bit for bit, as the IMAD path and the oracle."""
+    m = inputs.moments(N, beta, P)
+    with hk.Hankel(0) as h:
+        h.load(N, beta, P, m)
+        h.factor()
+        R0 = h.R()
+        h.set_update_path(1)
+        h.load(N, beta, P, m)
+        h.factor()
+        R1 = h.R()
+        assert h.stats()["limbprod_per_mac"] == h.stats()["W"] ** 2
+    assert R1 == R0
+    assert R1 == oracle.cholesky(m, N, P)
+
+
+def test_int8_tensor_path_signed_entries(hk):
+    pts = [(-3, 2), (-1, 2), (Fraction(1, 2), 1), (2, 1), (-5, 1), (-Fraction(3, 2), 2), (4, 1), (-7, 1)]
+    N, P = 8, 192
+    mom = []
+    for k in range(2 * N - 1):
+        v = sum((w * Fraction(x) ** k for x, w in pts), Fraction(0))
+        mom.append(oracle.mp_div(oracle.rne(v.numerator, 0, P * 4), oracle.rne(v.denominator, 0, P * 4), P))
+    with hk.Hankel(0) as h:
+        h.set_update_path(1)
+        h.load(N, (1, 1), P, mom)
+        h.factor()
+        R = h.R()
+    assert R == oracle.cholesky(mom, N, P)
