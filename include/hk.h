@@ -115,6 +115,37 @@ int hk_factor(hk_ctx *ctx, int *bad_row);
  * previous factorisation. */
 int hk_set_update_path(hk_ctx *ctx, int path);
 
+/* Options of a context (take effect at the next hk_factor):
+ *   HK_OPT_UPDATE_PATH      0 IMAD product scanning (default), 1 INT8 mma.sync
+ *   HK_OPT_KARATSUBA        Karatsuba levels of the IMAD update, 0..2 (default 2)
+ *   HK_OPT_GRAPH            1: capture each factorisation's launch sequence in a
+ *                           CUDA graph and replay it (default 0)
+ *   HK_OPT_AUTOTUNE         1: choose the update kernel's stripe width and chunk
+ *                           length per operand shape by timing the candidates on
+ *                           synthetic operands (cached per process; default 0,
+ *                           a cost model)
+ *   HK_OPT_PANEL_ROWS       rows per panel block, 1..256 (default 16)
+ *   HK_OPT_MAX_ITERS        step cap of hk_smallest_eig with iters = 0,
+ *                           1..100000 (default 200); keeps the factorisation
+ * None of the first five changes any result: every sum is exact. */
+enum { HK_OPT_UPDATE_PATH = 0, HK_OPT_KARATSUBA = 1, HK_OPT_GRAPH = 2, HK_OPT_AUTOTUNE = 3, HK_OPT_PANEL_ROWS = 4,
+       HK_OPT_MAX_ITERS = 5 };
+int hk_set_option(hk_ctx *ctx, int option, long long value);
+
+/* Solve `count` independent instances (moments[k] holds the 2N[k]-1 host
+ * moments of instance k at precision P[k]); beta is recorded for reporting.
+ * Workers (nthreads, <= 0 means 16) each own a context and a CUDA stream of
+ * ctx's device and take instances largest first (N^3 P^2); the options of ctx
+ * apply to all.  Per instance: status_out[k] (an hk_status; HK_ERR_NOT_PD means
+ * P[k] is too small), lambda_out[k] (caller limbs of P[k]/32 words) after
+ * `iters` steps of inverse iteration (0 = until converged), iters_out[k] (may
+ * be NULL) the steps taken, negated when iters = 0 and the step cap
+ * (HK_OPT_MAX_ITERS) ended the iteration before the convergence test was met.
+ * Returns HK_OK unless a worker could not start. */
+int hk_batch_solve(hk_ctx *ctx, int count, const int *N, const int *beta_num, const int *beta_den,
+                   const int *P, const hk_mp *const *moments, int iters, int nthreads,
+                   hk_mp *lambda_out, int *status_out, int *iters_out);
+
 /* Copy R (row-major packed upper triangle, N(N+1)/2 entries, entry (t, j),
  * j >= t, at index t*N - t*(t-1)/2 + (j - t)) to host hk_mp values whose
  * limbs arrays the caller provides. */
@@ -124,7 +155,8 @@ int hk_get_R(hk_ctx *ctx, hk_mp *R);
 int hk_get_R_flat(hk_ctx *ctx, int32_t *sign, int64_t *exp, uint32_t *limbs);
 
 /* Inverse iteration after hk_factor.  iters > 0: exactly that many steps.
- * iters == 0: until |lambda_t - lambda_{t-1}| <= 2^-136 lambda_t or 200 steps.
+ * iters == 0: until |lambda_t - lambda_{t-1}| <= 2^-136 lambda_t or the step
+ * cap (HK_OPT_MAX_ITERS, default 200); hk_get_stats out[5] says which.
  * *lambda_min receives lambda_T (caller-provided limbs[L]); *iters_used the
  * step count. */
 int hk_smallest_eig(hk_ctx *ctx, int iters, hk_mp *lambda_min, int *iters_used);
@@ -142,7 +174,8 @@ int hk_get_timings(hk_ctx *ctx, double *out, int n);
 /* Launch statistics of the last hk_factor + hk_smallest_eig: out[0] kernels
  * launched, out[1] exact-accumulation window width W in limbs, out[2]
  * widenings taken, out[3] Karatsuba levels of the factor update, out[4] limb
- * products the update executes per P-bit multiply-accumulate. */
+ * products the update executes per P-bit multiply-accumulate, out[5] 1 if the
+ * last hk_smallest_eig with iters = 0 met the convergence test. */
 int hk_get_stats(hk_ctx *ctx, int64_t *out, int n);
 
 /* ----- measurement hook ------------------------------------------------------
@@ -191,6 +224,41 @@ int hk_selftest_mp(int op, int L, const uint32_t *x, int nx, int64_t ex,
 int hk_mp_op_noalloc(int op, int L, const uint32_t *x, int nx, int64_t ex,
                      const uint32_t *y, int ny, int64_t ey, uint32_t *out, int64_t *eo,
                      void *stream);
+
+/* ----- precision predictor network ------------------------------------------
+ * The paper has no learned component.  Its precision requirement grows with N
+ * (Introduction; the K column of Table 2), and each P-bit multiply-accumulate
+ * costs about (P/32)^2 limb products, so the library carries a small network
+ * that predicts, from (N, beta), the working precision, log2 lambda_min and the
+ * iteration count; the caller verifies each prediction by a rerun at P + 1024
+ * bits.  Network: 2 -> 64 -> 64 -> 3, exact GELU z Phi(z) after both hidden
+ * layers, float32.  Parameters are one flat device array of HK_MLP_NPARAMS
+ * floats, row-major W[out][in]:
+ *   W1[64][2], b1[64], W2[64][64], b2[64], W3[3][64], b3[3].
+ * Loss of a batch of B samples (inputs x[B][2], targets t[B][3], per-output
+ * weights w[3]):  (1/B) sum_b sum_k w_k (y_bk - t_bk)^2.
+ * All pointers are DEVICE pointers; work runs asynchronously on `stream`
+ * (a cudaStream_t, NULL = legacy default).  Sums run in a fixed order, so every
+ * call is deterministic.  Errors: HK_ERR_ARG for B < 1 or a null pointer,
+ * HK_ERR_OOM for a work area below hk_mlp_workspace_bytes(B), HK_ERR_CUDA for a
+ * failed launch. */
+#define HK_MLP_NPARAMS 4547
+size_t hk_mlp_workspace_bytes(int B);
+/* y[B][3] = network(x). */
+int hk_mlp_forward(const float *params, const float *x, int B, float *y, void *stream);
+/* *loss and grad[HK_MLP_NPARAMS] (d loss / d params) by back-propagation. */
+int hk_mlp_loss_grad(const float *params, const float *x, const float *t, const float *w, int B,
+                     float *grad, float *loss, void *work, size_t work_bytes, void *stream);
+/* One Adam step (Kingma and Ba) on n parameters with moment arrays m, v,
+ * step index `step` >= 1 (bias corrections 1 - beta^step). */
+int hk_mlp_adam(float *params, const float *grad, float *m, float *v, int n, int step, float lr,
+                float beta1, float beta2, float eps, void *stream);
+/* `steps` full-batch Adam steps (indices step0+1 .. step0+steps) on the
+ * HK_MLP_NPARAMS parameters; loss_hist (device, may be NULL) receives the loss
+ * before each step.  grad is a device array of HK_MLP_NPARAMS floats. */
+int hk_mlp_train(float *params, float *m, float *v, float *grad, const float *x, const float *t,
+                 const float *w, int B, int steps, int step0, float lr, float beta1, float beta2,
+                 float eps, float *loss_hist, void *work, size_t work_bytes, void *stream);
 
 #ifdef __cplusplus
 }

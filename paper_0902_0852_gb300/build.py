@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhk.so")
-SOURCES = ["hk_api.cu", "hk_update.cu", "hk_panel.cu", "hk_solve.cu", "hk_selftest.cu", "hk_peaks.cu", "hk_update_i8.cu"]
+SOURCES = ["hk_api.cu", "hk_update.cu", "hk_panel.cu", "hk_solve.cu", "hk_selftest.cu", "hk_peaks.cu", "hk_update_i8.cu", "hk_batch.cu", "hk_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <vector>
@@ -84,6 +85,12 @@ struct hk_ctx {
   KarLayout kl{};
   int kar_levels = 2;
   int update_path = 0;       // 0: IMAD product scanning, 1: INT8 mma.sync
+  bool use_graph = false;    // capture each factorisation in a CUDA graph
+  cudaStream_t cap_stream = nullptr;  // capture stream when `stream` is a default stream
+  int max_iters = 200;       // step cap of hk_smallest_eig(iters = 0)
+  int eig_converged = 0;     // last hk_smallest_eig(iters = 0) met the convergence test
+  bool autotune = false;     // time candidate update schedules per shape
+  long long graph_launches = 0;
   int32_t *Asign = nullptr;
   uint32_t *recip = nullptr;
   long long *colsum = nullptr;
@@ -176,6 +183,110 @@ void ev_collect(hk_ctx *c) {
   c->evused = 0;
 }
 
+// ---- autotuner ---------------------------------------------------------------
+// Measured best (stripe width, chunk length) of the factor update per operand
+// shape, shared by all contexts of the process.
+std::mutex g_tune_mu;
+std::map<std::pair<long long, long long>, std::pair<int, int>> g_tune;
+
+__global__ void k_fill_random(uint32_t *x, size_t n, uint32_t seed) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)k * 2654435761u ^ seed;
+    h ^= h >> 16;
+    h *= 0x7feb352du;
+    h ^= h >> 15;
+    x[k] = h;
+  }
+}
+
+// Times every candidate schedule on a synthetic update (random operands; the
+// result is discarded) of the same sub-problem shapes: rows 64..79 of an
+// 80-row packed triangle against its first 64 rows.  Returns false on error.
+bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int upc_cap, int *uc_out,
+                       int *upc_out) {
+  const int Nt = 80, r0 = 64, r1 = 80;
+  const size_t NTt = (size_t)Nt * (Nt + 1) / 2;
+  uint32_t *A = nullptr;
+  int32_t *Asign = nullptr;
+  long long *cs = nullptr;
+  DevStatus *st = nullptr;
+  Unit *units = nullptr;
+  const int C = colsum_width(sub, nsub, 7) + 64;
+  long long nout = 0;
+  for (int i = r0; i < r1; i++) nout += Nt - i;
+  bool ok = cudaMalloc(&A, NTt * stride * 4) == cudaSuccess && cudaMalloc(&Asign, NTt * 4) == cudaSuccess &&
+            cudaMalloc(&cs, (size_t)nout * C * 8 * 2) == cudaSuccess && cudaMalloc(&st, sizeof(DevStatus)) == cudaSuccess;
+  const int cap = build_units(sub, nsub, 7, 14, nullptr, 0) + 16;  // the most units of any candidate
+  ok = ok && cudaMalloc(&units, (size_t)cap * sizeof(Unit)) == cudaSuccess;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ok) {
+    k_fill_random<<<256, 256, 0, c->stream>>>(A, NTt * stride, 12345u);
+    cudaMemsetAsync(Asign, 0, NTt * 4, c->stream);
+    cudaMemsetAsync(st, 0, sizeof(DevStatus), c->stream);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+  }
+  float best = 1e30f;
+  const int ucs[3] = {7, 9, 11};
+  for (int ui = 0; ui < 3 && ok; ui++) {
+    const int uc = ucs[ui];
+    for (int upc = 2 * uc; upc <= 8 * uc && upc <= upc_cap && ok; upc += uc) {
+      const int n = build_units(sub, nsub, uc, upc, nullptr, 0);
+      if (n > cap) continue;
+      std::vector<Unit> h(n);
+      build_units(sub, nsub, uc, upc, h.data(), n);
+      ok = cudaMemcpyAsync(units, h.data(), sizeof(Unit) * n, cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+      UpdParams up;
+      std::memset(&up, 0, sizeof(up));
+      up.mode = M_FACTOR;
+      up.N = Nt;
+      up.A = A;
+      up.Asign = Asign;
+      up.astride = stride;
+      up.cx = up.cy = stride;
+      up.uc = uc;
+      up.upc = upc;
+      up.nsub = nsub;
+      for (int k = 0; k < nsub; k++) up.sub[k] = sub[k];
+      up.r0 = r0;
+      up.ra = r0;
+      up.rb = r1;
+      up.nout = (int)nout;
+      up.t0 = 0;
+      up.t1 = r0;
+      up.tchunk = r0;
+      up.colsum = cs;
+      up.C = C;
+      up.units = units;
+      up.nunits = n;
+      up.st = st;
+      float t_best = 1e30f;
+      for (int rep = 0; rep < 3 && ok; rep++) {
+        cudaEventRecord(e0, c->stream);
+        ok = launch_update(up, c->stream) == cudaSuccess;
+        cudaEventRecord(e1, c->stream);
+        ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) t_best = std::min(t_best, ms);
+      }
+      if (ok && t_best < best) {
+        best = t_best;
+        *uc_out = uc;
+        *upc_out = upc;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(A);
+  cudaFree(Asign);
+  cudaFree(cs);
+  cudaFree(st);
+  cudaFree(units);
+  return ok && best < 1e30f;
+}
+
 // schedule of an update launch: the Karatsuba-expanded factor update
 // (levels > 0) or a plain contraction of widths (Wx, Wy)
 cudaError_t sched_for(hk_ctx *c, int Wx, int Wy, int levels, Sched *out) {
@@ -201,6 +312,31 @@ cudaError_t sched_for(hk_ctx *c, int Wx, int Wy, int levels, Sched *out) {
     sc.sub[0].tsign[0] = 1;
   }
   choose_schedule(sc.sub, sc.nsub, upc_cap, &sc.uc, &sc.upc);
+  if (c->autotune && !c->ws && Wx == Wy) {
+    // measured choice for factor-update shapes (cached for the process)
+    const auto tkey = std::make_pair((long long)Wx, (long long)levels);
+    bool have = false;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto t = g_tune.find(tkey);
+      if (t != g_tune.end()) {
+        sc.uc = t->second.first;
+        sc.upc = t->second.second;
+        have = true;
+      }
+    }
+    if (!have) {
+      KarLayout kl;
+      kar_layout(Wx, levels, KAR_GAP, &kl);
+      int uc = sc.uc, upc = sc.upc;
+      if (autotune_schedule(c, sc.sub, sc.nsub, levels > 0 ? kl.stride : Wx, upc_cap, &uc, &upc)) {
+        sc.uc = uc;
+        sc.upc = upc;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[tkey] = std::make_pair(uc, upc);
+      }
+    }
+  }
   sc.C = std::max(colsum_width(sc.sub, sc.nsub, sc.uc), ((Wx + Wy + 8 + 3) / 4) * 4);
   sc.n = build_units(sc.sub, sc.nsub, sc.uc, sc.upc, nullptr, 0);
   std::vector<Unit> h(sc.n);
@@ -264,6 +400,8 @@ __global__ void k_col_grid(int N, const long long *colU, int W, long long *colG)
 }
 
 // one attempt of the blocked factorisation with window width c->W
+int factor_enqueue(hk_ctx *c, const Sched &sc);
+
 int factor_attempt(hk_ctx *c) {
   const int N = c->N, L = c->L, W = c->W, nb = c->nb;
   const size_t NT = (size_t)N * (N + 1) / 2;
@@ -291,6 +429,49 @@ int factor_attempt(hk_ctx *c) {
     c->fac_levels = levels;
   }
   CK(reset_status(c));
+  if (!c->use_graph) return factor_enqueue(c, sc);
+  // capture the whole launch sequence of this factorisation in a CUDA graph
+  // and replay it (no host synchronisation happens inside the sequence)
+  const bool timing = c->timing;
+  c->timing = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  // the legacy and per-thread default streams cannot be captured: record on a
+  // private stream and launch the graph on the context's stream (recording
+  // runs nothing, so stream order is the launch's)
+  const cudaStream_t run = c->stream;
+  if (run == nullptr || run == cudaStreamLegacy || run == cudaStreamPerThread) {
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    c->stream = c->cap_stream;
+  }
+  const cudaError_t be = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (be != cudaSuccess) {
+    c->stream = run;
+    c->timing = timing;
+    return HK_ERR_CUDA;
+  }
+  const int rc = factor_enqueue(c, sc);
+  const cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+  c->stream = run;
+  c->timing = timing;
+  if (rc != HK_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  CK(ce);
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, c->stream);
+  if (exec) cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  CK(e);
+  c->graph_launches++;
+  return HK_OK;
+}
+
+// the factorisation's launch sequence (asynchronous on the context stream)
+int factor_enqueue(hk_ctx *c, const Sched &sc) {
+  const int N = c->N, L = c->L, W = c->W, nb = c->nb;
+  const int levels = c->update_path == 1 ? 0 : c->kar_levels;
   CK(launch_col_tops(N, L, c->top_margin, c->mom, c->colU, c->st, c->stream));
   k_col_grid<<<(N + 127) / 128, 128, 0, c->stream>>>(N, c->colU, W, c->colG);
   CK(cudaGetLastError());
@@ -649,6 +830,10 @@ bool converged(long long ea, const uint32_t *la, long long eb, const uint32_t *l
 
 extern "C" {
 
+int hk_batch_solve_impl(hk_ctx *parent, int device, const long long *opts, int count, const int *N,
+                        const int *bnum, const int *bden, const int *P, const hk_mp *const *moments, int iters,
+                        int nthreads, hk_mp *lambda_out, int *status_out, int *iters_out);
+
 const char *hk_strerror(int code) {
   switch (code) {
     case HK_OK: return "ok";
@@ -683,6 +868,7 @@ void hk_destroy(hk_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->sol_arena.release();
   c->fac_arena.release();
   c->base_arena.release();
@@ -869,6 +1055,47 @@ int hk_factor(hk_ctx *c, int *bad_row) {
   return result;
 }
 
+int hk_set_option(hk_ctx *c, int option, long long value) {
+  if (!c) return HK_ERR_ARG;
+  switch (option) {
+    case 0:  // update path
+      return hk_set_update_path(c, (int)value);
+    case 1:  // Karatsuba levels of the factor update
+      if (value < 0 || value > 2) return HK_ERR_ARG;
+      c->kar_levels = (int)value;
+      break;
+    case 2:  // capture factorisations in CUDA graphs
+      c->use_graph = value != 0;
+      break;
+    case 3:  // autotune update schedules
+      c->autotune = value != 0;
+      c->sched_cache.clear();
+      break;
+    case 4:  // panel block rows
+      if (value < 1 || value > 256) return HK_ERR_ARG;
+      c->nb = (int)value;
+      break;
+    case 5:  // step cap of the converging inverse iteration (R stays valid)
+      if (value < 1 || value > 100000) return HK_ERR_ARG;
+      c->max_iters = (int)value;
+      return HK_OK;
+    default:
+      return HK_ERR_ARG;
+  }
+  c->factored = false;
+  return HK_OK;
+}
+
+int hk_batch_solve(hk_ctx *c, int count, const int *N, const int *beta_num, const int *beta_den, const int *P,
+                   const hk_mp *const *moments, int iters, int nthreads, hk_mp *lambda_out, int *status_out,
+                   int *iters_out) {
+  if (!c || iters < 0) return HK_ERR_ARG;
+  const long long opts[6] = {c->update_path, c->kar_levels, c->use_graph ? 1 : 0, c->autotune ? 1 : 0, c->nb,
+                            c->max_iters};
+  return hk_batch_solve_impl(c, c->device, opts, count, N, beta_num, beta_den, P, moments, iters,
+                             nthreads > 0 ? nthreads : 16, lambda_out, status_out, iters_out);
+}
+
 int hk_set_update_path(hk_ctx *c, int path) {
   if (!c || path < 0 || path > 1) return HK_ERR_ARG;
   c->update_path = path;
@@ -910,7 +1137,8 @@ int hk_smallest_eig(hk_ctx *c, int iters, hk_mp *lambda_min, int *iters_used) {
   if (!c || iters < 0) return HK_ERR_ARG;
   if (!c->factored) return HK_ERR_STATE;
   cudaSetDevice(c->device);
-  const int T = iters > 0 ? iters : 200;
+  const int T = iters > 0 ? iters : c->max_iters;
+  c->eig_converged = 0;
   int rc = ensure_solve_buffers(c, T);
   if (rc) return rc;
   c->t_phase[2] = 0;
@@ -944,6 +1172,7 @@ int hk_smallest_eig(hk_ctx *c, int iters, hk_mp *lambda_min, int *iters_used) {
       CK(cudaMemcpyAsync(&scur, c->hist.sign + t, 4, cudaMemcpyDeviceToHost, c->stream));
       CK(cudaStreamSynchronize(c->stream));
       if (t > 0 && converged(ecur, cur.data(), eprev, prev.data(), L)) {
+        c->eig_converged = 1;
         t++;
         break;
       }
@@ -1013,9 +1242,10 @@ int hk_get_stats(hk_ctx *c, int64_t *out, int n) {
   const int ns = kar_subprobs(kl, sub);
   int64_t per_mac = 0;
   for (int k = 0; k < ns; k++) per_mac += (int64_t)sub[k].wx * sub[k].wy;
-  const int64_t v[5] = {c->launches, c->W, c->widenings, c->update_path == 1 ? 0 : c->kar_levels, per_mac};
-  for (int k = 0; k < n && k < 5; k++) out[k] = v[k];
-  for (int k = 5; k < n; k++) out[k] = 0;
+  const int64_t v[6] = {c->launches, c->W,      c->widenings, c->update_path == 1 ? 0 : c->kar_levels,
+                        per_mac,     c->eig_converged};
+  for (int k = 0; k < n && k < 6; k++) out[k] = v[k];
+  for (int k = 6; k < n; k++) out[k] = 0;
   return HK_OK;
 }
 

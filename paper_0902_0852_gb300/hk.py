@@ -25,6 +25,8 @@ EXPORTS = [
     "hk_load_moments", "hk_load_moments_flat", "hk_factor", "hk_get_R", "hk_get_R_flat",
     "hk_smallest_eig", "hk_get_history_flat", "hk_get_timings", "hk_get_stats", "hk_selftest_mp",
     "hk_probe_int_peaks", "hk_mp_op_noalloc", "hk_set_update_path",
+    "hk_set_option", "hk_batch_solve",
+    "hk_mlp_workspace_bytes", "hk_mlp_forward", "hk_mlp_loss_grad", "hk_mlp_adam", "hk_mlp_train",
 ]
 
 
@@ -69,8 +71,17 @@ def lib():
         L.hk_probe_int_peaks.argtypes = [i32, ctypes.POINTER(ctypes.c_double), i32]
         L.hk_mp_op_noalloc.argtypes = [i32, i32, vp, i32, i64, vp, i32, i64, vp, vp, vp]
         L.hk_set_update_path.argtypes = [vp, i32]
+        L.hk_set_option.argtypes = [vp, i32, i64]
+        L.hk_batch_solve.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp]
+        f32 = ctypes.c_float
+        L.hk_mlp_workspace_bytes.argtypes = [i32]
+        L.hk_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
+        L.hk_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, sz, vp]
+        L.hk_mlp_adam.argtypes = [vp, vp, vp, vp, i32, i32, f32, f32, f32, f32, vp]
+        L.hk_mlp_train.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, f32, f32, f32, f32, vp, vp, sz, vp]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype if name in ("hk_destroy", "hk_strerror") else i32
+        L.hk_mlp_workspace_bytes.restype = sz
         _lib = L
     return _lib
 
@@ -225,10 +236,10 @@ def hk_get_timings(ctx):
 
 
 def hk_get_stats(ctx):
-    out = (ctypes.c_int64 * 5)()
-    _check(lib().hk_get_stats(ctx, out, 5), "hk_get_stats")
+    out = (ctypes.c_int64 * 6)()
+    _check(lib().hk_get_stats(ctx, out, 6), "hk_get_stats")
     return {"launches": out[0], "W": out[1], "widenings": out[2], "karatsuba_levels": out[3],
-            "limbprod_per_mac": out[4]}
+            "limbprod_per_mac": out[4], "converged": out[5]}
 
 
 def hk_selftest_mp(op, L, x, ex=0, y=None, ey=0):
@@ -279,6 +290,52 @@ def hk_mp_op_noalloc(op, L, x, ex, y, ey, out, eo, stream=None):
                                   ctypes.c_void_p(s)), "hk_mp_op_noalloc")
 
 
+HK_OPT_UPDATE_PATH, HK_OPT_KARATSUBA, HK_OPT_GRAPH, HK_OPT_AUTOTUNE, HK_OPT_PANEL_ROWS, HK_OPT_MAX_ITERS = range(6)
+
+
+def hk_set_option(ctx, option, value):
+    _check(lib().hk_set_option(ctx, option, int(value)), "hk_set_option")
+
+
+def hk_batch_solve(ctx, instances, iters=0, nthreads=16):
+    """instances: list of (N, (p, q), P, moments).  Returns a list of
+    (status, lambda (n, e) or None, iterations used)."""
+    count = len(instances)
+    Ns = np.array([x[0] for x in instances], dtype=np.int32)
+    bn = np.array([x[1][0] for x in instances], dtype=np.int32)
+    bd = np.array([x[1][1] for x in instances], dtype=np.int32)
+    Ps = np.array([x[2] for x in instances], dtype=np.int32)
+    keep = []
+    mom_ptrs = (ctypes.POINTER(HkMp) * count)()
+    lam = (HkMp * count)()
+    lam_limbs = []
+    for k, (N, beta, P, moments) in enumerate(instances):
+        sign, exp, limbs = pack(moments, P)
+        arr = (HkMp * len(moments))()
+        for i in range(len(moments)):
+            arr[i].sign = int(sign[i])
+            arr[i].exp = int(exp[i])
+            arr[i].limbs = limbs[i].ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+        keep.append((limbs, arr))
+        mom_ptrs[k] = ctypes.cast(arr, ctypes.POINTER(HkMp))
+        ll = np.zeros(P // 32, dtype=np.uint32)
+        lam_limbs.append(ll)
+        lam[k].limbs = ll.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+    status = np.zeros(count, dtype=np.int32)
+    used = np.zeros(count, dtype=np.int32)
+    _check(lib().hk_batch_solve(ctx, count, _ptr(Ns), _ptr(bn), _ptr(bd), _ptr(Ps),
+                                ctypes.cast(mom_ptrs, ctypes.c_void_p), iters, nthreads,
+                                ctypes.cast(lam, ctypes.c_void_p), _ptr(status), _ptr(used)), "hk_batch_solve")
+    out = []
+    for k in range(count):
+        if status[k] == HK_OK:
+            v = unpack(np.array([lam[k].sign]), np.array([lam[k].exp]), lam_limbs[k].reshape(1, -1))[0]
+        else:
+            v = None
+        out.append((int(status[k]), v, int(used[k])))
+    return out
+
+
 class Hankel:
     """Convenience wrapper: one context, one problem."""
 
@@ -310,6 +367,9 @@ class Hankel:
     def factor(self):
         hk_factor(self.ctx)
 
+    def set_option(self, option, value):
+        hk_set_option(self.ctx, option, value)
+
     def set_update_path(self, path):
         """0: IMAD product scanning (default), 1: INT8 tensor instruction."""
         _check(lib().hk_set_update_path(self.ctx, path), "hk_set_update_path")
@@ -328,3 +388,42 @@ class Hankel:
 
     def stats(self):
         return hk_get_stats(self.ctx)
+
+
+HK_MLP_NPARAMS = 4547
+
+
+def _dp(t):
+    """Device pointer of a CUDA tensor (None -> NULL)."""
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream):
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
+
+
+def hk_mlp_workspace_bytes(B):
+    return int(lib().hk_mlp_workspace_bytes(B))
+
+
+def hk_mlp_forward(params, x, y, stream=None):
+    """params float32[HK_MLP_NPARAMS], x float32[B, 2], y float32[B, 3]: CUDA tensors."""
+    _check(lib().hk_mlp_forward(_dp(params), _dp(x), x.shape[0], _dp(y), _stream(stream)), "hk_mlp_forward")
+
+
+def hk_mlp_loss_grad(params, x, t, w, grad, loss, work, stream=None):
+    _check(lib().hk_mlp_loss_grad(_dp(params), _dp(x), _dp(t), _dp(w), x.shape[0], _dp(grad), _dp(loss),
+                                  _dp(work), work.numel() * work.element_size(), _stream(stream)),
+           "hk_mlp_loss_grad")
+
+
+def hk_mlp_adam(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().hk_mlp_adam(_dp(params), _dp(grad), _dp(m), _dp(v), params.numel(), step, lr, beta1, beta2,
+                             eps, _stream(stream)), "hk_mlp_adam")
+
+
+def hk_mlp_train(params, m, v, grad, x, t, w, steps, step0, lr, work, loss_hist=None, beta1=0.9, beta2=0.999,
+                 eps=1e-8, stream=None):
+    _check(lib().hk_mlp_train(_dp(params), _dp(m), _dp(v), _dp(grad), _dp(x), _dp(t), _dp(w), x.shape[0], steps,
+                              step0, lr, beta1, beta2, eps, _dp(loss_hist), _dp(work),
+                              work.numel() * work.element_size(), _stream(stream)), "hk_mlp_train")
