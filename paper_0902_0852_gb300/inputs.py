@@ -94,9 +94,10 @@ def moment(k, beta, P):
             return _round_int(num, P)
         return _round_ratio(num, den, P)
     consts = _gamma_consts()
-    if (a, p) not in consts:
+    g = gcd(a, p)
+    if (a // g, p // g) not in consts:
         raise ValueError(f"no stored constant Gamma({a}/{p}) for beta={p}/{q}")
-    F, G = consts[(a, p)]
+    F, G = consts[(a // g, p // g)]
     if F < P + 160:
         raise ValueError(f"Gamma({a}/{p}) stored to {F} bits, P={P} needs {P + 160}")
     c = q
@@ -112,7 +113,58 @@ def moment(k, beta, P):
 
 def moments(N, beta, P):
     """The 2N-1 moments m_0..m_{2N-2} of the order-N matrix, rounded to P bits."""
-    return [moment(k, beta, P) for k in range(2 * N - 1)]
+    return MomentSource(N, beta).at(P)
+
+
+class MomentSource:
+    """The exact rational parts of the 2N-1 moments of one (N, beta), built
+    once with running products (O(N) big-integer products instead of O(N^2)),
+    then rounded to any precision P: ``at(P)`` equals ``[moment(k, beta, P)]``.
+    Meant for precision searches that need the same matrix at many P."""
+
+    def __init__(self, N, beta):
+        self.N = N
+        self.p, self.q = as_ratio(beta)
+        p, q = self.p, self.q
+        parts = []
+        run = {}          # residue a -> (n0, q * prod_{i<n0} (a + i p))
+        fm, fval = 0, 1   # running factorial fm! = fval
+        for k in range(2 * N - 1):
+            n0, a = divmod(q * (1 + k), p)
+            if a == 0:
+                while fm < n0 - 1:
+                    fm += 1
+                    fval *= fm
+                parts.append((None, q * fval, p))
+            else:
+                n_prev, c = run.get(a, (0, q))
+                for i in range(n_prev, n0):
+                    c *= a + i * p
+                run[a] = (n0, c)
+                g = gcd(a, p)
+                parts.append(((a // g, p // g), c, n0))
+        self.parts = parts
+
+    def at(self, P):
+        consts = None
+        out = []
+        for key, c, n in self.parts:
+            if key is None:
+                out.append(_round_int(c, P) if n == 1 else _round_ratio(c, n, P))
+                continue
+            if consts is None:
+                consts = _gamma_consts()
+            if key not in consts:
+                raise ValueError(f"no stored constant Gamma({key[0]}/{key[1]}) for beta={self.p}/{self.q}")
+            F, G = consts[key]
+            if F < P + 160:
+                raise ValueError(f"Gamma({key[0]}/{key[1]}) stored to {F} bits, P={P} needs {P + 160}")
+            d = self.p ** (n + 1) << F
+            lo = _round_ratio(G * c, d, P)
+            if lo != _round_ratio((G + 1) * c, d, P):
+                raise ArithmeticError(f"a moment of beta={self.p}/{self.q} is too close to a rounding boundary")
+            out.append(lo)
+        return out
 
 
 def batched_instances(count=64, seed=0):
