@@ -1,0 +1,84 @@
+"""Generates the precision predictor's training tuples with the method itself,
+trains the network on the device, and evaluates it on held-out instances.
+Runs on a machine with the GPU (the solves and the training use the library's
+kernels).  Writes, into --out (default: this directory):
+
+  predictor_tuples.json  (N, beta) -> required bits, log2 lambda_min, iterations
+  predictor.json         trained parameters, scalings and safety margin
+  predictor_eval.json    held-out instances: conservative solve vs predicted
+                         and verified solve (precisions, seconds, agreement)
+
+Instances: training N ~ U{32..512}, beta ~ U[0.6, 4] snapped to the rational
+grid of predictor.beta_grid() (seed 1); held-out N ~ U{513..800}, same beta
+law (seed 2).
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from paper_0902_0852_gb300 import build, predictor as pr  # noqa: E402
+
+
+def log(msg):
+    print(f"[{time.strftime('%H:%M:%S')}] {msg}", flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=1024)
+    ap.add_argument("--heldout", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--out", default=HERE)
+    ap.add_argument("--tuples", default=None, help="reuse an existing tuples file")
+    ap.add_argument("--workers", type=int, default=12)
+    args = ap.parse_args()
+    build.build()
+    os.makedirs(args.out, exist_ok=True)
+    if args.tuples:
+        tuples = json.load(open(args.tuples))["tuples"]
+    else:
+        inst = pr.sample_instances(args.train, 1, 32, 512)
+        t0 = time.time()
+        tuples = pr.generate(inst, workers=args.workers, log=log)
+        meta = dict(generator="paper_0902_0852_gb300/data/make_predictor.py", count=len(inst), seed=1,
+                    N_range=[32, 512], beta="U[0.6,4] snapped to beta_grid()", seconds=round(time.time() - t0, 1),
+                    agree_bits=pr.AGREE_BITS, delta=pr.DELTA)
+        with open(os.path.join(args.out, "predictor_tuples.json"), "w") as f:
+            json.dump(dict(meta=meta, tuples=tuples), f, indent=0)
+        log(f"{len(tuples)} tuples in {meta['seconds']} s")
+    model = pr.Predictor()
+    hist = model.fit(tuples, steps=args.steps, log=log)
+    d = model.to_json()
+    d["loss_first_last"] = [float(hist[0]), float(hist[-1])]
+    with open(os.path.join(args.out, "predictor.json"), "w") as f:
+        json.dump(d, f)
+    rows = []
+    for N, beta in pr.sample_instances(args.heldout, 2, 513, 800):
+        c = pr.solve_conservative(N, beta)
+        v = pr.solve_verified(N, beta, model)
+        agree = pr.rel_err_bits(v["lam"], c["lam"]) if (v["lam"] and c["lam"]) else None
+        rows.append(dict(N=N, beta=list(beta), P_cons=c["P"], cons_seconds=round(c["seconds"], 4),
+                         cons_iters=c["iters"], cons_converged=c["converged"], P_pred=v["P"], tried=v["tried"],
+                         pred_seconds=round(v["seconds"], 4), pred_iters=v["iters"], T_budget=v["T"],
+                         verified=v["verified"], agree_bits=None if agree is None else min(agree, 1e9),
+                         log2_lambda=pr.log2_value(c["lam"]) if c["lam"] else None))
+        log(f"held-out N={N} beta={beta}: P {c['P']} -> {v['P']} ({v['tried']}), "
+            f"{c['seconds']:.2f}s -> {v['seconds']:.2f}s, agree {agree}")
+    tc = sum(r["cons_seconds"] for r in rows)
+    tp = sum(r["pred_seconds"] for r in rows)
+    summary = dict(instances=len(rows), conservative_seconds=round(tc, 3), predicted_seconds=round(tp, 3),
+                   gain=round(tc / tp, 3) if tp else None, all_verified=all(r["verified"] for r in rows),
+                   min_agree_bits=min((r["agree_bits"] for r in rows if r["agree_bits"] is not None), default=None),
+                   escalated=sum(len(r["tried"]) > 2 for r in rows))
+    with open(os.path.join(args.out, "predictor_eval.json"), "w") as f:
+        json.dump(dict(summary=summary, rows=rows), f, indent=0)
+    log(json.dumps(summary))
+
+
+if __name__ == "__main__":
+    main()

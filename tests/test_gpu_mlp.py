@@ -79,8 +79,11 @@ def test_adam_matches_reference(env):
     P, G, Mm, V = (_dev(torch, a) for a in (p, g, m, v))
     hk.hk_mlp_adam(P, G, Mm, V, step=7, lr=3e-3)
     torch.cuda.synchronize()
+    # the device takes its hyperparameters as float32: give the reference the
+    # same values (1 - beta is then exact in float32 as well)
+    f = lambda x: float(np.float32(x))  # noqa: E731
     pw, mw, vw = mlp.adam_step(p.astype(np.float64), g.astype(np.float64), m.astype(np.float64),
-                               v.astype(np.float64), 7, 3e-3)
+                               v.astype(np.float64), 7, f(3e-3), f(0.9), f(0.999), f(1e-8))
     # float32 rounding of b1 m + (1 - b1) g is relative to the operands, not
     # to the (possibly cancelling) sum
     scale_m = 0.9 * np.abs(m.astype(np.float64)) + 0.1 * np.abs(g.astype(np.float64))

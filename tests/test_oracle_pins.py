@@ -144,7 +144,8 @@ def test_beta1_closed_form(N, P):
 # beta = 7/4 worked example (Introduction, second N = 4 matrix)
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("beta", [(7, 4), (3, 4), (3, 2), (2, 1), (3, 1), (1, 2), (1, 3)])
+@pytest.mark.parametrize("beta", [(7, 4), (3, 4), (3, 2), (2, 1), (3, 1), (1, 2), (1, 3), (4, 3), (4, 5), (5, 2), (5, 8),
+                                  (7, 11), (3, 5), (2, 3)])
 def test_moments_match_mpmath(beta):
     """The rational-recurrence moment generator equals RNE of an independent
     mpmath evaluation of Gamma((1+k)/beta)/beta at 3P bits."""
