@@ -175,7 +175,9 @@ int hk_get_timings(hk_ctx *ctx, double *out, int n);
  * launched, out[1] exact-accumulation window width W in limbs, out[2]
  * widenings taken, out[3] Karatsuba levels of the factor update, out[4] limb
  * products the update executes per P-bit multiply-accumulate, out[5] 1 if the
- * last hk_smallest_eig with iters = 0 met the convergence test. */
+ * last hk_smallest_eig with iters = 0 met the convergence test, out[6] and
+ * out[7] the largest and mean window width in limbs of the solution vectors
+ * in that hk_smallest_eig (the exact products of a solve cost W x that width). */
 int hk_get_stats(hk_ctx *ctx, int64_t *out, int n);
 
 /* ----- measurement hook ------------------------------------------------------

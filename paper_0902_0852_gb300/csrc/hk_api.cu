@@ -46,7 +46,7 @@ struct Arena {
 };
 
 struct EvPair {
-  cudaEvent_t a, b;
+  cudaEvent_t a = nullptr, b = nullptr;
 };
 
 // unit table and schedule of the update kernel for one operand shape
@@ -88,6 +88,7 @@ struct hk_ctx {
   bool use_graph = false;    // capture each factorisation in a CUDA graph
   cudaStream_t cap_stream = nullptr;  // capture stream when `stream` is a default stream
   int max_iters = 200;       // step cap of hk_smallest_eig(iters = 0)
+  long long wv_max = 0, wv_sum = 0, wv_count = 0;  // solve window widths of the last eig
   int eig_converged = 0;     // last hk_smallest_eig(iters = 0) met the convergence test
   bool autotune = false;     // time candidate update schedules per shape
   long long graph_launches = 0;
@@ -161,8 +162,12 @@ void ev_begin(hk_ctx *c, int kind) {
   if (!c->timing) return;
   if (c->evused == c->evpool.size()) {
     EvPair p;
-    cudaEventCreate(&p.a);
-    cudaEventCreate(&p.b);
+    if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) {
+      // no more events: stop timing this context rather than record on a bad handle
+      if (p.a) cudaEventDestroy(p.a);
+      c->timing = false;
+      return;
+    }
     c->evpool.push_back(p);
   }
   if (c->evkind.size() < c->evpool.size()) c->evkind.resize(c->evpool.size());
@@ -170,7 +175,7 @@ void ev_begin(hk_ctx *c, int kind) {
   cudaEventRecord(c->evpool[c->evused].a, c->stream);
 }
 void ev_end(hk_ctx *c) {
-  if (!c->timing) return;
+  if (!c->timing || c->evused >= c->evpool.size()) return;
   cudaEventRecord(c->evpool[c->evused].b, c->stream);
   c->evused++;
 }
@@ -650,6 +655,11 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
       }
       sp.nosum = have_known ? 0 : 1;
       const int Wv = std::max(4, round4((top - h + 31) / 32));
+      if (have_known) {
+        c->wv_max = std::max<long long>(c->wv_max, Wv);
+        c->wv_sum += Wv;
+        c->wv_count++;
+      }
       Sched sc;
       CK(sched_for(c, W, Wv, 0, &sc));
       const int Cs = sc.C;
@@ -722,13 +732,14 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
       }
       ev_end(c);
       DevStatus st = read_status(c);
-      if (st.code != ST_OK) return st.code == ST_NOT_PD ? HK_ERR_NOT_PD : HK_ERR_CUDA;
+      ev_collect(c);  // the stream is idle: fold the block's events into the phase times
       if (st.timeout) return HK_ERR_TIMEOUT;
       if (st.range_fail) {
         margin = margin * 4 + st.need_bits;
         CK(reset_status(c));
         continue;
       }
+      if (st.code != ST_OK) return st.code == ST_NOT_PD ? HK_ERR_NOT_PD : HK_ERR_CUDA;
       break;
     }
   }
@@ -873,8 +884,8 @@ void hk_destroy(hk_ctx *c) {
   c->fac_arena.release();
   c->base_arena.release();
   for (auto &p : c->evpool) {
-    cudaEventDestroy(p.a);
-    cudaEventDestroy(p.b);
+    if (p.a) cudaEventDestroy(p.a);
+    if (p.b) cudaEventDestroy(p.b);
   }
   delete c;
 }
@@ -1139,6 +1150,7 @@ int hk_smallest_eig(hk_ctx *c, int iters, hk_mp *lambda_min, int *iters_used) {
   cudaSetDevice(c->device);
   const int T = iters > 0 ? iters : c->max_iters;
   c->eig_converged = 0;
+  c->wv_max = c->wv_sum = c->wv_count = 0;
   int rc = ensure_solve_buffers(c, T);
   if (rc) return rc;
   c->t_phase[2] = 0;
@@ -1194,6 +1206,7 @@ int hk_smallest_eig(hk_ctx *c, int iters, hk_mp *lambda_min, int *iters_used) {
   DevStatus st = read_status(c);
   if (st.code == ST_NOT_PD) return HK_ERR_NOT_PD;
   if (st.timeout) return HK_ERR_TIMEOUT;
+  if (st.range_fail || st.code != ST_OK) return HK_ERR_RANGE;
   const int used = std::min(t, T);
   c->hist_count = used;
   if (iters_used) *iters_used = used;
@@ -1242,10 +1255,16 @@ int hk_get_stats(hk_ctx *c, int64_t *out, int n) {
   const int ns = kar_subprobs(kl, sub);
   int64_t per_mac = 0;
   for (int k = 0; k < ns; k++) per_mac += (int64_t)sub[k].wx * sub[k].wy;
-  const int64_t v[6] = {c->launches, c->W,      c->widenings, c->update_path == 1 ? 0 : c->kar_levels,
-                        per_mac,     c->eig_converged};
-  for (int k = 0; k < n && k < 6; k++) out[k] = v[k];
-  for (int k = 6; k < n; k++) out[k] = 0;
+  const int64_t v[8] = {c->launches,
+                        c->W,
+                        c->widenings,
+                        c->update_path == 1 ? 0 : c->kar_levels,
+                        per_mac,
+                        c->eig_converged,
+                        c->wv_max,
+                        c->wv_count ? c->wv_sum / c->wv_count : 0};
+  for (int k = 0; k < n && k < 8; k++) out[k] = v[k];
+  for (int k = 8; k < n; k++) out[k] = 0;
   return HK_OK;
 }
 

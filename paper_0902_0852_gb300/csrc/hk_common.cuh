@@ -33,6 +33,9 @@ struct MpArr {
 HK_DEV void raise_range(DevStatus *st, long long need) {
   atomicAdd(&st->range_fail, 1);
   atomicMax(&st->need_bits, need);
+  // later kernels of the sequence test the code on entry and skip: nothing
+  // runs on an entry that was not written
+  atomicCAS(&st->code, ST_OK, ST_RANGE);
 }
 
 }  // namespace hk

@@ -6,6 +6,13 @@
 
 namespace hk {
 
+// Let kernel `fn` use all the opt-in shared memory of the current device, once
+// per (kernel, device) under a process-wide lock.  Launchers call it instead of
+// setting the limit to their own size: with several host threads launching the
+// same kernel with different sizes, per-size updates would race (one thread
+// lowering the limit while another launches with more).
+cudaError_t allow_dynamic_smem(const void *fn);
+
 // ---- exact contraction (hk_update.cu) ----------------------------------------
 // Stripe width (columns per thread) and p-steps per work unit.
 constexpr int UC = 9;          // default stripe width (result columns per thread)

@@ -11,6 +11,7 @@
 // network costs a few microseconds per step at B = 4096, far below any
 // roofline that would reward tensor cores, so plain FP32 FMAs are used.
 #include "hk.h"
+#include "hk_internal.h"
 
 #include <cuda_runtime.h>
 #include <math.h>
@@ -216,11 +217,8 @@ __global__ void k_adam(float *__restrict__ prm, const float *__restrict__ g, flo
 int ntiles(int B) { return (B + MT - 1) / MT; }
 
 int smem_attr() {
-  // cheap host call; setting it on every entry keeps it right on every device
-  if (cudaFuncSetAttribute(k_mlp_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_mlp_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES) !=
-          cudaSuccess)
+  if (hk::allow_dynamic_smem((const void *)k_mlp_tile<true>) != cudaSuccess ||
+      hk::allow_dynamic_smem((const void *)k_mlp_tile<false>) != cudaSuccess)
     return HK_ERR_CUDA;
   return HK_OK;
 }

@@ -284,19 +284,13 @@ cudaError_t launch_col_tops(int N, int L, long long top_margin, MpArr mom, long 
   return cudaGetLastError();
 }
 
-static cudaError_t set_smem(const void *fn, size_t bytes, size_t *done) {
-  if (bytes > 48 * 1024 && bytes > *done) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    *done = bytes;
-  }
-  return cudaSuccess;
+static cudaError_t set_smem(const void *fn, size_t bytes) {
+  return bytes > 48 * 1024 ? allow_dynamic_smem(fn) : cudaSuccess;
 }
 
 cudaError_t launch_diag(const PanelParams &p, int i, cudaStream_t s) {
-  static size_t done = 0;
   const size_t smem = panel_smem_diag(p.L, p.C);
-  cudaError_t e = set_smem((const void *)k_diag, smem, &done);
+  cudaError_t e = set_smem((const void *)k_diag, smem);
   if (e != cudaSuccess) return e;
   k_diag<<<1, NT_DIAG, smem, s>>>(p, i);
   return cudaGetLastError();
@@ -304,9 +298,8 @@ cudaError_t launch_diag(const PanelParams &p, int i, cudaStream_t s) {
 
 cudaError_t launch_offdiag(const PanelParams &p, int i, cudaStream_t s) {
   if (i + 1 >= p.N) return cudaSuccess;
-  static size_t done = 0;
   const size_t smem = panel_smem_row(p.L, p.C);
-  cudaError_t e = set_smem((const void *)k_offdiag, smem, &done);
+  cudaError_t e = set_smem((const void *)k_offdiag, smem);
   if (e != cudaSuccess) return e;
   k_offdiag<<<p.N - i - 1, NT_ROW, smem, s>>>(p, i);
   return cudaGetLastError();

@@ -301,21 +301,15 @@ __global__ void k_set_ones(int n, MpArr v, int L) {
   }
 }
 
-cudaError_t set_smem(const void *fn, size_t bytes, size_t *done) {
-  if (bytes > 48 * 1024 && bytes > *done) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    *done = bytes;
-  }
-  return cudaSuccess;
+cudaError_t set_smem(const void *fn, size_t bytes) {
+  return bytes > 48 * 1024 ? allow_dynamic_smem(fn) : cudaSuccess;
 }
 
 }  // namespace
 
 cudaError_t launch_solve_entry(const SolveParams &p, int i, cudaStream_t s) {
-  static size_t done = 0;
   const size_t smem = ssmem_size(p.L, p.C, false);
-  cudaError_t e = set_smem((const void *)k_solve_entry, smem, &done);
+  cudaError_t e = set_smem((const void *)k_solve_entry, smem);
   if (e != cudaSuccess) return e;
   k_solve_entry<<<1, NT_SOLVE, smem, s>>>(p, i);
   return cudaGetLastError();
@@ -336,9 +330,8 @@ cudaError_t launch_vec_align(int n0, int n1, MpArr v, int L, const long long *of
 
 cudaError_t launch_lambda(int L, const long long *colsum, int C, long long hv, long long hw, MpArr lam,
                           int slot, DevStatus *st, cudaStream_t s) {
-  static size_t done = 0;
   const size_t smem = ssmem_size(L, C, true);
-  cudaError_t e = set_smem((const void *)k_lambda, smem, &done);
+  cudaError_t e = set_smem((const void *)k_lambda, smem);
   if (e != cudaSuccess) return e;
   k_lambda<<<1, NT_LAM, smem, s>>>(L, colsum, C, hv, hw, lam, slot, st);
   return cudaGetLastError();

@@ -34,6 +34,8 @@
 #include <algorithm>
 #include <climits>
 #include <cstdlib>
+#include <mutex>
+#include <set>
 #include <vector>
 
 namespace hk {
@@ -319,6 +321,26 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
 // host-side schedule helpers
 // ---------------------------------------------------------------------------
 
+cudaError_t allow_dynamic_smem(const void *fn) {
+  static std::mutex mu;
+  static std::set<std::pair<const void *, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({fn, dev})) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e != cudaSuccess) return e;
+  done.insert({fn, dev});
+  return cudaSuccess;
+}
+
 void kar_layout(int W, int levels, int gap, KarLayout *kl) {
   KarLayout k{};
   k.levels = levels;
@@ -495,11 +517,9 @@ cudaError_t launch_uc(const UpdParams &p, cudaStream_t s) {
   const int Xsz = ((p.cx + xpadr(p.upc) + 3) / 4) * 4;
   const int Ysz = ((ypadl(UCT, p.upc) + p.cy + ypadr(UCT) + 3) / 4) * 4;
   const size_t smem = (size_t)USTAGES * (Xsz + Ysz) * 4 + 2 * USTAGES * 8 + 4 * (USTAGES + 4);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_update<UCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) {
+    cudaError_t e = allow_dynamic_smem((const void *)k_update<UCT>);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   const int nz = (p.t1 - p.t0 + p.tchunk - 1) / p.tchunk;
   dim3 grid((p.nunits + UNT - 1) / UNT, p.nout, nz);

@@ -232,11 +232,9 @@ cudaError_t launch_update_i8(const UpdParams &p, cudaStream_t s) {
   if (p.nout <= 0 || p.t1 <= p.t0) return cudaSuccess;
   const int W = p.astride;
   const size_t smem = update_i8_smem(W);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_update_i8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) {
+    cudaError_t e = allow_dynamic_smem((const void *)k_update_i8);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   long long noct = 0;
   for (int i = p.ra; i < p.rb; i++) noct += (p.N - i + 7) / 8;

@@ -236,10 +236,10 @@ def hk_get_timings(ctx):
 
 
 def hk_get_stats(ctx):
-    out = (ctypes.c_int64 * 6)()
-    _check(lib().hk_get_stats(ctx, out, 6), "hk_get_stats")
+    out = (ctypes.c_int64 * 8)()
+    _check(lib().hk_get_stats(ctx, out, 8), "hk_get_stats")
     return {"launches": out[0], "W": out[1], "widenings": out[2], "karatsuba_levels": out[3],
-            "limbprod_per_mac": out[4], "converged": out[5]}
+            "limbprod_per_mac": out[4], "converged": out[5], "solve_wv_max": out[6], "solve_wv_mean": out[7]}
 
 
 def hk_selftest_mp(op, L, x, ex=0, y=None, ey=0):
