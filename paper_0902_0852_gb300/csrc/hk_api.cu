@@ -6,6 +6,7 @@
 #include "hk_internal.h"
 
 #include <algorithm>
+#include <cstdio>
 #include <climits>
 #include <cstdlib>
 #include <cstring>
@@ -95,6 +96,7 @@ struct hk_ctx {
   int32_t *Asign = nullptr;
   uint32_t *recip = nullptr;
   long long *colsum = nullptr;
+  long long A_len = 0, Aexp_len = 0, colsum_len = 0;  // sizes of A, Aexp (limbs) and colsum (entries)
   int fac_N = 0, fac_L = 0, fac_W = 0, fac_levels = -1;  // shape of the factor buffers
   std::map<std::pair<long long, long long>, Sched> sched_cache;
   // solve buffers
@@ -131,6 +133,34 @@ int cuda_status(cudaError_t e) {
     cudaError_t e_ = (x);                      \
     if (e_ != cudaSuccess) return cuda_status(e_); \
   } while (0)
+
+#ifdef HK_CHECKED
+// Checked build: after every launch, wait for it and report a fault or a
+// failed bounds check with the launch that caused it (stderr), then stop.
+int dbg_after(hk_ctx *c, const char *what, long long a, long long b) {
+  const cudaError_t e = cudaStreamSynchronize(c->stream);
+  const cudaError_t l = cudaGetLastError();
+  DevStatus s{};
+  if (e == cudaSuccess) cudaMemcpy(&s, c->st, sizeof(s), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess || l != cudaSuccess || s.check_site) {
+    fprintf(stderr,
+            "[hk checked] %s (%lld, %lld) N=%d L=%d W=%d: sync=%s last=%s check_site=%d a=%lld b=%lld\n", what,
+            a, b, c->N, c->L, c->W, cudaGetErrorString(e), cudaGetErrorString(l), s.check_site, s.check_a,
+            s.check_b);
+    return e != cudaSuccess || l != cudaSuccess ? HK_ERR_CUDA : HK_ERR_RANGE;
+  }
+  return HK_OK;
+}
+#define DBG(c, what, a, b)                               \
+  do {                                                   \
+    const int r_ = dbg_after((c), (what), (a), (b));     \
+    if (r_ != HK_OK) return r_;                          \
+  } while (0)
+#else
+#define DBG(c, what, a, b) \
+  do {                     \
+  } while (0)
+#endif
 
 cudaError_t arena_get(hk_ctx *c, Arena &a, void **p, size_t bytes) {
   if (c->ws) {
@@ -262,6 +292,8 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
       up.tchunk = r0;
       up.colsum = cs;
       up.C = C;
+      up.a_len = (long long)NTt * stride;
+      up.colsum_len = nout * C * 2;
       up.units = units;
       up.nunits = n;
       up.st = st;
@@ -295,7 +327,7 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
 // schedule of an update launch: the Karatsuba-expanded factor update
 // (levels > 0) or a plain contraction of widths (Wx, Wy)
 cudaError_t sched_for(hk_ctx *c, int Wx, int Wy, int levels, Sched *out) {
-  const auto key = std::make_pair((long long)Wx * 4096 + Wy, (long long)levels);
+  const auto key = std::make_pair(((long long)Wx << 32) | (long long)(unsigned)Wy, (long long)levels);
   auto it = c->sched_cache.find(key);
   if (it != c->sched_cache.end()) {
     *out = it->second;
@@ -428,6 +460,9 @@ int factor_attempt(hk_ctx *c) {
     CK(alloc(c, c->fac_arena, &c->colsum, (size_t)maxout * c->C));
     c->Aexp = nullptr;
     if (levels > 0) CK(alloc(c, c->fac_arena, &c->Aexp, NT * (size_t)c->kl.stride));
+    c->A_len = (long long)NT * W;
+    c->Aexp_len = levels > 0 ? (long long)NT * c->kl.stride : 0;
+    c->colsum_len = maxout * c->C;
     c->fac_N = N;
     c->fac_L = L;
     c->fac_W = W;
@@ -478,7 +513,9 @@ int factor_enqueue(hk_ctx *c, const Sched &sc) {
   const int N = c->N, L = c->L, W = c->W, nb = c->nb;
   const int levels = c->update_path == 1 ? 0 : c->kar_levels;
   CK(launch_col_tops(N, L, c->top_margin, c->mom, c->colU, c->st, c->stream));
+  DBG(c, "col_tops", N, L);
   k_col_grid<<<(N + 127) / 128, 128, 0, c->stream>>>(N, c->colU, W, c->colG);
+  DBG(c, "col_grid", N, W);
   CK(cudaGetLastError());
   c->launches += 2;
 
@@ -494,6 +531,8 @@ int factor_enqueue(hk_ctx *c, const Sched &sc) {
   pp.Asign = c->Asign;
   pp.recip = c->recip;
   pp.colsum = c->colsum;
+  pp.colsum_len = c->colsum_len;
+  pp.aexp_len = c->Aexp_len;
   pp.st = c->st;
   pp.kl = c->kl;
   pp.Aexp = c->Aexp;
@@ -507,6 +546,8 @@ int factor_enqueue(hk_ctx *c, const Sched &sc) {
   up.astride = levels > 0 ? c->kl.stride : W;
   up.cx = up.cy = up.astride;
   up.colsum = c->colsum;
+  up.a_len = levels > 0 ? c->Aexp_len : c->A_len;
+  up.colsum_len = c->colsum_len;
   fill_sched(up, sc);
   up.st = c->st;
   const long long cta_per_out = (sc.n + UNT - 1) / UNT;
@@ -527,13 +568,16 @@ int factor_enqueue(hk_ctx *c, const Sched &sc) {
       up.tchunk = pick_tchunk(r0, cta_per_out * nout, target);
       ev_begin(c, 0);
       CK(c->update_path == 1 ? launch_update_i8(up, c->stream) : launch_update(up, c->stream));
+      DBG(c, "factor update", up.ra, up.t1);
       ev_end(c);
       c->launches++;
     }
     for (int i = r0; i < r1; i++) {
       ev_begin(c, 1);
       CK(launch_diag(pp, i, c->stream));
+      DBG(c, "diag", i, 0);
       CK(launch_offdiag(pp, i, c->stream));
+      DBG(c, "offdiag", i, 0);
       ev_end(c);
       c->launches += (i + 1 < N) ? 2 : 1;
       if (i + 1 < r1) {
@@ -545,6 +589,7 @@ int factor_enqueue(hk_ctx *c, const Sched &sc) {
         up.tchunk = 1;
         ev_begin(c, 0);
         CK(c->update_path == 1 ? launch_update_i8(up, c->stream) : launch_update(up, c->stream));
+        DBG(c, "factor update", up.ra, up.t1);
         ev_end(c);
         c->launches++;
       }
@@ -638,6 +683,7 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
         sub.exp += k0;
         sub.limbs += (size_t)k0 * L;
         CK(launch_vec_exprange(k1 - k0, sub, L, c->colG + k0, back ? 1 : 0, c->d_range, c->stream));
+        DBG(c, "solve exprange", B0, k1 - k0);
         c->launches++;
         long long hh[2];
         CK(cudaMemcpyAsync(hh, c->d_range, sizeof(hh), cudaMemcpyDeviceToHost, c->stream));
@@ -671,12 +717,15 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
       sp.C = Cs;
       sp.h = h;
       sp.colsum = c->colsum_s;
+      sp.colsum_len = (long long)c->colsum_s_cap;
+      sp.vec_len = (long long)c->vec_cap;
       sp.r0 = B0;
       CK(cudaMemsetAsync(c->colsum_s, 0, sizeof(long long) * (size_t)(B1 - B0) * Cs, c->stream));
       ev_begin(c, 2);
       if (have_known) {
         CK(launch_vec_align(k0, k1, out, L, c->colG, back ? 1 : 0, h, Wv, c->vecA, c->vecAsign, c->st,
-                            c->stream));
+                            (long long)c->vec_cap, c->stream));
+        DBG(c, "solve vec_align", B0, Wv);
         c->launches++;
       }
       UpdParams up;
@@ -693,6 +742,9 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
       up.cy = Wv;
       up.r0 = B0;
       up.colsum = c->colsum_s;
+      up.a_len = c->A_len;
+      up.vy_len = (long long)c->vec_cap;
+      up.colsum_len = (long long)c->colsum_s_cap;
       fill_sched(up, sc);
       up.st = c->st;
       const long long cta_per_out = (sc.n + UNT - 1) / UNT;
@@ -705,6 +757,7 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
         up.t1 = k1;
         up.tchunk = pick_tchunk(k1 - k0, cta_per_out * (B1 - B0), target);
         CK(launch_update(up, c->stream));
+        DBG(c, "gemv/dot update", up.ra, up.t0);
         c->launches++;
       }
       sp.h = h;
@@ -712,6 +765,7 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
         const int i = back ? B1 - 1 - s : B0 + s;
         // the first entry of each solve has no sum: the kernel takes G from the rhs
         CK(launch_solve_entry(sp, i, c->stream));
+        DBG(c, "solve entry", i, Wv);
         c->launches++;
         const bool more = back ? (i > B0) : (i + 1 < B1);
         if (more) {
@@ -727,6 +781,7 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
           up.t1 = i + 1;
           up.tchunk = 1;
           CK(launch_update(up, c->stream));
+          DBG(c, "gemv/dot update", up.ra, up.t0);
           c->launches++;
         }
       }
@@ -762,8 +817,12 @@ int rayleigh(hk_ctx *c, int slot) {
   rc = ensure_vec(c, Wd, Cd, 2);
   if (rc) return rc;
   ev_begin(c, 2);
-  CK(launch_vec_align(0, N, c->v, L, nullptr, 0, lov, Wd, c->vecA, c->vecAsign, c->st, c->stream));
-  CK(launch_vec_align(0, N, c->w, L, nullptr, 0, low, Wd, c->vecB, c->vecBsign, c->st, c->stream));
+  CK(launch_vec_align(0, N, c->v, L, nullptr, 0, lov, Wd, c->vecA, c->vecAsign, c->st, (long long)c->vec_cap,
+                      c->stream));
+  DBG(c, "lambda vec_align v", N, Wd);
+  CK(launch_vec_align(0, N, c->w, L, nullptr, 0, low, Wd, c->vecB, c->vecBsign, c->st, (long long)c->vec_cap,
+                      c->stream));
+  DBG(c, "lambda vec_align w", N, Wd);
   CK(cudaMemsetAsync(c->colsum_s, 0, sizeof(long long) * 2 * Cd, c->stream));
   UpdParams up;
   std::memset(&up, 0, sizeof(up));
@@ -779,12 +838,16 @@ int rayleigh(hk_ctx *c, int slot) {
   up.t0 = 0;
   up.t1 = N;
   up.colsum = c->colsum_s;
+  up.vx_len = up.vy_len = (long long)c->vec_cap;
+  up.colsum_len = (long long)c->colsum_s_cap;
   fill_sched(up, sc);
   up.st = c->st;
   const long long cta_per_out = (sc.n + UNT - 1) / UNT;
   up.tchunk = pick_tchunk(N, cta_per_out * 2, 6LL * sm_count(c) * 3);
   CK(launch_update(up, c->stream));
-  CK(launch_lambda(L, c->colsum_s, Cd, lov, low, c->hist, slot, c->st, c->stream));
+  DBG(c, "gemv/dot update", up.ra, up.t0);
+  CK(launch_lambda(L, c->colsum_s, Cd, lov, low, c->hist, slot, c->st, (long long)c->colsum_s_cap, c->stream));
+  DBG(c, "lambda", slot, Cd);
   ev_end(c);
   c->launches += 4;
   return HK_OK;

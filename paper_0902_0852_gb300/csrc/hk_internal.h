@@ -78,6 +78,7 @@ struct UpdParams {
   int tchunk;              // t per CTA (z dimension)
   long long *colsum;       // [outputs][C] signed 64-bit column sums (accumulated)
   int C;
+  long long a_len, vx_len, vy_len, colsum_len;  // buffer sizes (limbs / entries), for checked builds
   const Unit *units;
   int nunits;
   DevStatus *st;
@@ -108,6 +109,7 @@ struct PanelParams {
   const long long *colsum; // [block outputs][C]
   int r0;                  // block base row
   DevStatus *st;
+  long long colsum_len, aexp_len;  // buffer sizes, for checked builds
 };
 cudaError_t launch_col_tops(int N, int L, long long top_margin, MpArr mom, long long *colU, DevStatus *st,
                             cudaStream_t s);
@@ -132,15 +134,16 @@ struct SolveParams {
   int back;                // 0 forward, 1 back
   int nosum;               // first entry of a solve: no sum, no aligned copy
   DevStatus *st;
+  long long vec_len, colsum_len;  // buffer sizes, for checked builds
 };
 cudaError_t launch_solve_entry(const SolveParams &p, int i, cudaStream_t s);
 cudaError_t launch_vec_exprange(int n, MpArr v, int L, const long long *colU, int scaled,
                                 long long *out2, cudaStream_t s);
 cudaError_t launch_vec_align(int n0, int n1, MpArr v, int L, const long long *colU, int scaled,
                              long long h, int Wv, uint32_t *vecA, int32_t *vecAsign,
-                             DevStatus *st, cudaStream_t s);
+                             DevStatus *st, long long vec_len, cudaStream_t s);
 cudaError_t launch_lambda(int L, const long long *colsum, int C, long long hv, long long hw,
-                          MpArr lam, int slot, DevStatus *st, cudaStream_t s);
+                          MpArr lam, int slot, DevStatus *st, long long colsum_len, cudaStream_t s);
 cudaError_t launch_vec_normalise(int n, MpArr w, MpArr v, int L, cudaStream_t s);
 cudaError_t launch_set_ones(int n, MpArr v, int L, cudaStream_t s);
 

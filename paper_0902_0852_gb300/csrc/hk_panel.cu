@@ -173,9 +173,12 @@ HK_DEV void expand_entry(const uint32_t *a, const KarLayout &kl, uint32_t *dst, 
 }
 
 __global__ void __launch_bounds__(NT_DIAG) k_diag(PanelParams p, int i) {
-  if (p.st->code != ST_OK) return;
+  if (block_status(p.st) != ST_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RowSmem s;
+  if (!HK_CHECK(p.st, carve(nullptr, p.L, p.C, true, nullptr) <= dynamic_smem_bytes(), 11,
+                carve(nullptr, p.L, p.C, true, nullptr), dynamic_smem_bytes()))
+    return;
   carve(smem_raw, p.L, p.C, true, &s);
   mp::Work w = work_of(s);
   const int L = p.L, N = p.N;
@@ -185,6 +188,10 @@ __global__ void __launch_bounds__(NT_DIAG) k_diag(PanelParams p, int i) {
   const long long crow = k * N - (k * (i + p.r0 - 1)) / 2;
   const long long *colrow = p.colsum + crow * p.C;
   const int mk = 2 * i;
+  if (!HK_CHECK(p.st, crow >= 0 && crow * p.C + p.C <= p.colsum_len, 12, crow * p.C + p.C, p.colsum_len) ||
+      !HK_CHECK(p.st, p.kl.levels == 0 || (tri_idx(i, i, N) + 1) * p.kl.stride <= p.aexp_len, 13,
+                (tri_idx(i, i, N) + 1) * p.kl.stride, p.aexp_len))
+    return;
   int nZ = 0;
   const int sgn = form_exact<NT_DIAG>(s, colrow, p.C, p.mom.sign[mk], p.mom.exp[mk],
                                       p.mom.limbs + (long long)mk * L, L, 2 * gi, p.st, &nZ);
@@ -222,9 +229,12 @@ __global__ void __launch_bounds__(NT_DIAG) k_diag(PanelParams p, int i) {
 }
 
 __global__ void __launch_bounds__(NT_ROW) k_offdiag(PanelParams p, int i) {
-  if (p.st->code != ST_OK) return;
+  if (block_status(p.st) != ST_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RowSmem s;
+  if (!HK_CHECK(p.st, carve(nullptr, p.L, p.C, false, nullptr) <= dynamic_smem_bytes(), 14,
+                carve(nullptr, p.L, p.C, false, nullptr), dynamic_smem_bytes()))
+    return;
   carve(smem_raw, p.L, p.C, false, &s);
   mp::Work w = work_of(s);
   const int L = p.L, N = p.N;
@@ -235,6 +245,11 @@ __global__ void __launch_bounds__(NT_ROW) k_offdiag(PanelParams p, int i) {
   const long long crow = k * N - (k * (i + p.r0 - 1)) / 2 + (j - i);
   const long long *colrow = p.colsum + crow * p.C;
   const int mk = i + j;
+  if (!HK_CHECK(p.st, j < N, 15, j, N) ||
+      !HK_CHECK(p.st, crow >= 0 && crow * p.C + p.C <= p.colsum_len, 16, crow * p.C + p.C, p.colsum_len) ||
+      !HK_CHECK(p.st, p.kl.levels == 0 || (tri_idx(i, j, N) + 1) * p.kl.stride <= p.aexp_len, 17,
+                (tri_idx(i, j, N) + 1) * p.kl.stride, p.aexp_len))
+    return;
   int nZ = 0;
   const int sgn = form_exact<NT_ROW>(s, colrow, p.C, p.mom.sign[mk], p.mom.exp[mk],
                                      p.mom.limbs + (long long)mk * L, L, gi + gj, p.st, &nZ);

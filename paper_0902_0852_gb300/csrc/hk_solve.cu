@@ -104,9 +104,15 @@ HK_DEV int form_exact_s(SSmem &s, const long long *colrow, int C, int32_t sv, lo
 
 // one solve entry i: out_i = RNE(RNE(rhs_i - sum) / R_ii); aligned copy in vecA[i]
 __global__ void __launch_bounds__(NT_SOLVE) k_solve_entry(SolveParams p, int i) {
-  if (p.st->code != ST_OK) return;
+  if (block_status(p.st) != ST_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SSmem s;
+  if (!HK_CHECK(p.st, ssmem_size(p.L, p.C, false) <= dynamic_smem_bytes(), 21, ssmem_size(p.L, p.C, false),
+                dynamic_smem_bytes()) ||
+      !HK_CHECK(p.st, (long long)(i - p.r0 + 1) * p.C <= p.colsum_len && i >= p.r0, 22,
+                (long long)(i - p.r0 + 1) * p.C, p.colsum_len) ||
+      !HK_CHECK(p.st, p.nosum || (long long)(i + 1) * p.Wv <= p.vec_len, 23, (long long)(i + 1) * p.Wv, p.vec_len))
+    return;
   scarve(smem_raw, p.L, p.C, false, &s);
   mp::Work w = swork(s);
   const int L = p.L, N = p.N;
@@ -193,8 +199,9 @@ __global__ void k_vec_exprange(int n, MpArr v, int L, const long long *off, long
 
 // vecA[k] = v_k * 2^(e_k + off_k - h) as Wv limbs, k in [n0, n1) (one block per entry)
 __global__ void k_vec_align(int n0, MpArr v, int L, const long long *off, long long h, int Wv,
-                            uint32_t *vecA, int32_t *vecAsign, DevStatus *st) {
+                            uint32_t *vecA, int32_t *vecAsign, DevStatus *st, long long vec_len) {
   const int k = n0 + blockIdx.x;
+  if (!HK_CHECK(st, (long long)(k + 1) * Wv <= vec_len, 41, (long long)(k + 1) * Wv, vec_len)) return;
   const uint32_t *src = v.limbs + (long long)k * L;
   uint32_t *dst = vecA + (long long)k * Wv;
   __shared__ int nz_s;
@@ -225,9 +232,14 @@ __global__ void k_vec_align(int n0, MpArr v, int L, const long long *off, long l
 
 // lambda = RNE(RNE(vv 2^(2 hv)) / RNE(vw 2^(hv + hw))) from the two DOT outputs
 __global__ void __launch_bounds__(NT_LAM) k_lambda(int L, const long long *colsum, int C, long long hv,
-                                                   long long hw, MpArr lam, int slot, DevStatus *st) {
+                                                   long long hw, MpArr lam, int slot, DevStatus *st,
+                                                   long long colsum_len) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SSmem s;
+  if (!HK_CHECK(st, ssmem_size(L, C, true) <= dynamic_smem_bytes(), 31, ssmem_size(L, C, true),
+                dynamic_smem_bytes()) ||
+      !HK_CHECK(st, 2LL * C <= colsum_len, 32, 2LL * C, colsum_len))
+    return;
   scarve(smem_raw, L, C, true, &s);
   mp::Work w = swork(s);
   // RNE(<v,w>) -> s.rm (divisor)
@@ -322,18 +334,19 @@ cudaError_t launch_vec_exprange(int n, MpArr v, int L, const long long *off, int
 }
 
 cudaError_t launch_vec_align(int n0, int n1, MpArr v, int L, const long long *off, int scaled, long long h,
-                             int Wv, uint32_t *vecA, int32_t *vecAsign, DevStatus *st, cudaStream_t s) {
+                             int Wv, uint32_t *vecA, int32_t *vecAsign, DevStatus *st, long long vec_len,
+                             cudaStream_t s) {
   if (n1 <= n0) return cudaSuccess;
-  k_vec_align<<<n1 - n0, 128, 0, s>>>(n0, v, L, scaled ? off : nullptr, h, Wv, vecA, vecAsign, st);
+  k_vec_align<<<n1 - n0, 128, 0, s>>>(n0, v, L, scaled ? off : nullptr, h, Wv, vecA, vecAsign, st, vec_len);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lambda(int L, const long long *colsum, int C, long long hv, long long hw, MpArr lam,
-                          int slot, DevStatus *st, cudaStream_t s) {
+                          int slot, DevStatus *st, long long colsum_len, cudaStream_t s) {
   const size_t smem = ssmem_size(L, C, true);
   cudaError_t e = set_smem((const void *)k_lambda, smem);
   if (e != cudaSuccess) return e;
-  k_lambda<<<1, NT_LAM, smem, s>>>(L, colsum, C, hv, hw, lam, slot, st);
+  k_lambda<<<1, NT_LAM, smem, s>>>(L, colsum, C, hv, hw, lam, slot, st, colsum_len);
   return cudaGetLastError();
 }
 

@@ -167,7 +167,10 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
   int *sneg = reinterpret_cast<int *>(empty + USTAGES);  // sign of the stage's product
   volatile int *abort_flag = sneg + USTAGES;
 
-  if (p.st->code != ST_OK) return;  // an earlier step failed: nothing to do
+  if (block_status(p.st) != ST_OK) return;  // an earlier step failed: nothing to do
+  if (!HK_CHECK(p.st, (size_t)USTAGES * (Xsz + Ysz) * 4 + 2 * USTAGES * 8 + 4 * (USTAGES + 4) <= dynamic_smem_bytes(),
+                1, (size_t)USTAGES * (Xsz + Ysz) * 4, dynamic_smem_bytes()))
+    return;
 
   const int o = blockIdx.y;
   int oi, oj;
@@ -218,6 +221,23 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
         }
         if (*abort_flag) break;
         const Operands op = operands(p, oi, oj, tb + it);
+#ifdef HK_CHECKED
+        {
+          const uint32_t *bx = p.mode == M_DOT ? p.Vx : p.A;
+          const long long lx = p.mode == M_DOT ? p.vx_len : p.a_len;
+          const uint32_t *by = p.mode == M_FACTOR ? p.A : (p.mode == M_DOT && oj == 0 ? p.Vx : p.Vy);
+          const long long ly = p.mode == M_FACTOR ? p.a_len : (p.mode == M_DOT && oj == 0 ? p.vx_len : p.vy_len);
+          const long long ox = op.x - bx, oy = op.y - by;
+          if (!HK_CHECK(p.st, ox >= 0 && ox + p.cx <= lx, 2, ox, lx) ||
+              !HK_CHECK(p.st, oy >= 0 && oy + p.cy <= ly, 3, oy, ly) ||
+              !HK_CHECK(p.st, ((uintptr_t)op.x & 15) == 0 && ((uintptr_t)op.y & 15) == 0 && (bytesX & 15) == 0 &&
+                                  (bytesY & 15) == 0,
+                        4, (long long)((uintptr_t)op.x & 15), (long long)((uintptr_t)op.y & 15))) {
+            *abort_flag = 1;
+            break;
+          }
+        }
+#endif
         uint32_t *xs = bufs + (size_t)s * (Xsz + Ysz);
         uint32_t *ys = xs + Xsz + YPADL;
         sneg[s] = op.neg;
@@ -237,11 +257,22 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
 
   // ---------------- compute warps ----------------
   const int u = blockIdx.x * UNT + threadIdx.x;
-  const bool active = u < p.nunits;
+  bool active = u < p.nunits;
   const Unit un = active ? p.units[u] : Unit{0, 0};
   const int sp = (un.d0 >> 24) & 0xff;
   const int d0 = un.d0 & 0xffffff, p0 = un.p0;
   const int xoff = p.sub[sp].xoff, yoff = p.sub[sp].yoff;
+#ifdef HK_CHECKED
+  if (active) {
+    // every shared-memory word the unit reads lies in its stage's X or Y tile
+    const long long xlo = xoff + p0, xhi = xoff + p0 + p.upc - 1;
+    const long long ylo = YPADL + yoff + d0 - p0 - p.upc + 1, yhi = YPADL + yoff + d0 - p0 + UC - 1;
+    if (!HK_CHECK(p.st, sp < p.nsub, 5, sp, p.nsub) || !HK_CHECK(p.st, xlo >= 0 && xhi < Xsz, 6, xhi, Xsz) ||
+        !HK_CHECK(p.st, ylo >= 0 && yhi < Ysz, 7, ylo < 0 ? ylo : yhi, Ysz) ||
+        !HK_CHECK(p.st, crow * p.C + p.C <= p.colsum_len, 8, crow * p.C + p.C, p.colsum_len))
+      active = false;
+  }
+#endif
   uint32_t c0[UC], c1[UC], c2[UC];
 #pragma unroll
   for (int m = 0; m < UC; m++) c0[m] = c1[m] = c2[m] = 0;

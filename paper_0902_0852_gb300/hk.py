@@ -15,7 +15,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libhk.so")
+# HK_CHECKED=1 selects the diagnosis build (device bounds checks, a
+# synchronisation after every launch); see build.py
+_LIB_PATH = os.path.join(_HERE, "libhk_checked.so" if os.environ.get("HK_CHECKED") == "1" else "libhk.so")
 _lib = None
 
 HK_OK, HK_ERR_ARG, HK_ERR_NOT_PD, HK_ERR_CUDA, HK_ERR_OOM, HK_ERR_TIMEOUT, HK_ERR_STATE, HK_ERR_RANGE = range(8)
