@@ -141,7 +141,10 @@ int dbg_after(hk_ctx *c, const char *what, long long a, long long b) {
   const cudaError_t e = cudaStreamSynchronize(c->stream);
   const cudaError_t l = cudaGetLastError();
   DevStatus s{};
-  if (e == cudaSuccess) cudaMemcpy(&s, c->st, sizeof(s), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) {
+    cudaMemcpyAsync(&s, c->st, sizeof(s), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+  }
   if (e != cudaSuccess || l != cudaSuccess || s.check_site) {
     fprintf(stderr,
             "[hk checked] %s (%lld, %lld) N=%d L=%d W=%d: sync=%s last=%s check_site=%d a=%lld b=%lld\n", what,
@@ -380,7 +383,10 @@ cudaError_t sched_for(hk_ctx *c, int Wx, int Wy, int levels, Sched *out) {
   build_units(sc.sub, sc.nsub, sc.uc, sc.upc, h.data(), sc.n);
   cudaError_t e = alloc(c, c->base_arena, &sc.units, (size_t)sc.n);
   if (e != cudaSuccess) return e;
-  e = cudaMemcpy(sc.units, h.data(), sizeof(Unit) * sc.n, cudaMemcpyHostToDevice);
+  // on the context's stream: a plain cudaMemcpy runs on the legacy default
+  // stream, which a non-blocking context stream does not wait for, and for
+  // pageable memory it returns before the transfer has landed
+  e = cudaMemcpyAsync(sc.units, h.data(), sizeof(Unit) * sc.n, cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return e;
   c->sched_cache[key] = sc;
   *out = sc;
@@ -1120,6 +1126,10 @@ int hk_factor(hk_ctx *c, int *bad_row) {
       result = HK_ERR_NOT_PD;
       break;
     }
+    if (st.code != ST_OK) {  // a failed device check
+      result = HK_ERR_CUDA;
+      break;
+    }
     c->factored = true;
     result = HK_OK;
     break;
@@ -1269,7 +1279,8 @@ int hk_smallest_eig(hk_ctx *c, int iters, hk_mp *lambda_min, int *iters_used) {
   DevStatus st = read_status(c);
   if (st.code == ST_NOT_PD) return HK_ERR_NOT_PD;
   if (st.timeout) return HK_ERR_TIMEOUT;
-  if (st.range_fail || st.code != ST_OK) return HK_ERR_RANGE;
+  if (st.range_fail) return HK_ERR_RANGE;
+  if (st.code != ST_OK) return HK_ERR_CUDA;
   const int used = std::min(t, T);
   c->hist_count = used;
   if (iters_used) *iters_used = used;

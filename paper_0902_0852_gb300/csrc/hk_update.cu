@@ -261,13 +261,16 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
   const Unit un = active ? p.units[u] : Unit{0, 0};
   const int sp = (un.d0 >> 24) & 0xff;
   const int d0 = un.d0 & 0xffffff, p0 = un.p0;
-  const int xoff = p.sub[sp].xoff, yoff = p.sub[sp].yoff;
+  // a unit table entry must name one of this launch's sub-problems (always
+  // checked: a bad entry would index the operand tiles with wrong offsets)
+  if (active && sp >= p.nsub) active = check_fail(p.st, 5, sp, p.nsub);
+  const int xoff = p.sub[active ? sp : 0].xoff, yoff = p.sub[active ? sp : 0].yoff;
 #ifdef HK_CHECKED
   if (active) {
     // every shared-memory word the unit reads lies in its stage's X or Y tile
     const long long xlo = xoff + p0, xhi = xoff + p0 + p.upc - 1;
     const long long ylo = YPADL + yoff + d0 - p0 - p.upc + 1, yhi = YPADL + yoff + d0 - p0 + UC - 1;
-    if (!HK_CHECK(p.st, sp < p.nsub, 5, sp, p.nsub) || !HK_CHECK(p.st, xlo >= 0 && xhi < Xsz, 6, xhi, Xsz) ||
+    if (!HK_CHECK(p.st, xlo >= 0 && xhi < Xsz, 6, xhi, Xsz) ||
         !HK_CHECK(p.st, ylo >= 0 && yhi < Ysz, 7, ylo < 0 ? ylo : yhi, Ysz) ||
         !HK_CHECK(p.st, crow * p.C + p.C <= p.colsum_len, 8, crow * p.C + p.C, p.colsum_len))
       active = false;
