@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--P", type=int, default=24576)
     ap.add_argument("--iters", type=int, default=0, help="0 = until converged (2^-136)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-predicted", action="store_true",
+                    help="skip the predicted-precision time-to-lambda comparison (after the timed region)")
     return ap.parse_args()
 
 
@@ -293,8 +295,10 @@ def main():
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     peak = n_sm * 64 * max_mhz * 1e6 / 2 / 1e12
-    traffic = (UPDATE_TRAFFIC_BYTES_PER_LIMBPROD * limbprod / args.steps /
-               (recs[-1][3]["launches"] or 1)) if UPDATE_TRAFFIC_BYTES_PER_LIMBPROD else None
+    # per update launch, averaged like `achieved`: one big update per 16-row
+    # block after the first plus one in-block update per row -> N - 1 launches
+    traffic = (UPDATE_TRAFFIC_BYTES_PER_LIMBPROD * (N - 1) * N * (N + 1) // 6 * st["limbprod_per_mac"] /
+               (N - 1)) if UPDATE_TRAFFIC_BYTES_PER_LIMBPROD else None
     n_lam, e_lam = lam
     # decimal rendering of lambda (n * 2^e) with 10 significant digits
     lg = math.log10(abs(n_lam)) + e_lam * math.log10(2)
@@ -329,10 +333,35 @@ def main():
         "clocks": clocks,
         "gpu_launches": sum(r[3]["launches"] for r in recs),
     }
+    out["solve_window_limbs"] = {"max": st.get("solve_wv_max"), "mean": st.get("solve_wv_mean"), "W": st["W"]}
     if cpu is not None:
         out["cpu_baseline"] = cpu
     h.close()
+    if not args.no_predicted and world == 1:
+        out["time_to_lambda_predicted"] = predicted_comparison(N, beta)
     print(json.dumps(out))
+
+
+def predicted_comparison(N, beta):
+    """Time to a verified lambda_min at the precision the trained predictor
+    picks (solve at P, verify at P + 1024, escalate on disagreement) against
+    the method alone at the conservative precision; both through the library,
+    timed around the library calls (which synchronise), after the benchmark's
+    timed region.  The two lambdas must agree to 2^-128."""
+    from paper_0902_0852_gb300 import predictor as pr
+    path = os.path.join(ROOT, "paper_0902_0852_gb300", "data", "predictor.json")
+    if not os.path.exists(path):
+        return None
+    model = pr.load_default()
+    c = pr.solve_conservative(N, beta)
+    v = pr.solve_verified(N, beta, model)
+    agree = pr.rel_err_bits(v["lam"], c["lam"]) if v["lam"] and c["lam"] else None
+    return {"P_conservative": c["P"], "t_conservative_s": round(c["seconds"], 4), "iters_conservative": c["iters"],
+            "P_predicted": v["P"], "precisions_run": v["tried"], "t_predicted_verified_s": round(v["seconds"], 4),
+            "iters_predicted": v["iters"], "verified": v["verified"],
+            "agree_bits": None if agree is None else min(agree, 1e9),
+            "speedup": round(c["seconds"] / v["seconds"], 3) if v["seconds"] else None,
+            "update_path": "IMAD (the INT8 mma.sync path is slower on GB300)"}
 
 
 if __name__ == "__main__":
