@@ -57,6 +57,8 @@ struct Sched {
   int nsub;
   SubProb sub[MAX_SUB];
   int C;  // column sums per output
+  int nxb, maxlen;  // per-block operand windows (Karatsuba), see UpdParams
+  int xlo[MAX_XB], xlen[MAX_XB];
 };
 
 // gap between Karatsuba pieces: covers the zero padding a unit reads past a
@@ -89,6 +91,7 @@ struct hk_ctx {
   bool use_graph = false;    // capture each factorisation in a CUDA graph
   cudaStream_t cap_stream = nullptr;  // capture stream when `stream` is a default stream
   int max_iters = 200;       // step cap of hk_smallest_eig(iters = 0)
+  long long fuse_ww = 160000;  // solve blocks run in one launch when W * Wv is at most this
   long long wv_max = 0, wv_sum = 0, wv_count = 0;  // solve window widths of the last eig
   int eig_converged = 0;     // last hk_smallest_eig(iters = 0) met the convergence test
   bool autotune = false;     // time candidate update schedules per shape
@@ -103,6 +106,8 @@ struct hk_ctx {
   MpArr v{}, y{}, w{}, hist{};
   int hist_cap = 0, hist_count = 0;
   uint32_t *vecA = nullptr, *vecB = nullptr;
+  uint32_t *vecAexp = nullptr;  // Karatsuba expansion of vecA (solves on the factor's window)
+  size_t vecAexp_cap = 0;       // limbs
   int32_t *vecAsign = nullptr, *vecBsign = nullptr;
   size_t vec_cap = 0;  // limbs per vector buffer
   long long *colsum_s = nullptr;
@@ -276,12 +281,14 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
       ok = cudaMemcpyAsync(units, h.data(), sizeof(Unit) * n, cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
       UpdParams up;
       std::memset(&up, 0, sizeof(up));
+      const int maxlen = operand_windows(sub, nsub, h.data(), n, ((KAR_GAP + 3) / 4) * 4, stride, up.xlo, up.xlen);
+      up.nxb = maxlen > 0 ? (n + UNT - 1) / UNT : 0;
       up.mode = M_FACTOR;
       up.N = Nt;
       up.A = A;
       up.Asign = Asign;
       up.astride = stride;
-      up.cx = up.cy = stride;
+      up.cx = up.cy = up.nxb ? maxlen : stride;
       up.uc = uc;
       up.upc = upc;
       up.nsub = nsub;
@@ -381,6 +388,14 @@ cudaError_t sched_for(hk_ctx *c, int Wx, int Wy, int levels, Sched *out) {
   sc.n = build_units(sc.sub, sc.nsub, sc.uc, sc.upc, nullptr, 0);
   std::vector<Unit> h(sc.n);
   build_units(sc.sub, sc.nsub, sc.uc, sc.upc, h.data(), sc.n);
+  sc.nxb = 0;
+  sc.maxlen = 0;
+  if (levels > 0) {
+    KarLayout kl;
+    kar_layout(Wx, levels, KAR_GAP, &kl);
+    sc.maxlen = operand_windows(sc.sub, sc.nsub, h.data(), sc.n, kl.G, kl.stride, sc.xlo, sc.xlen);
+    if (sc.maxlen > 0) sc.nxb = (sc.n + UNT - 1) / UNT;
+  }
   cudaError_t e = alloc(c, c->base_arena, &sc.units, (size_t)sc.n);
   if (e != cudaSuccess) return e;
   // on the context's stream: a plain cudaMemcpy runs on the legacy default
@@ -401,6 +416,12 @@ void fill_sched(UpdParams &up, const Sched &sc) {
   up.nsub = sc.nsub;
   for (int k = 0; k < sc.nsub; k++) up.sub[k] = sc.sub[k];
   up.C = sc.C;
+  up.nxb = sc.nxb;
+  for (int k = 0; k < sc.nxb; k++) {
+    up.xlo[k] = sc.xlo[k];
+    up.xlen[k] = sc.xlen[k];
+  }
+  if (sc.nxb > 0) up.cx = up.cy = sc.maxlen;  // stage size: the longest block window
 }
 
 int sm_count(hk_ctx *c) {
@@ -620,7 +641,7 @@ int ensure_solve_buffers(hk_ctx *c, int hist_need) {
   return HK_OK;
 }
 
-int ensure_vec(hk_ctx *c, int Wv, int Cs, int rows) {
+int ensure_vec(hk_ctx *c, int Wv, int Cs, int rows, int kar_stride = 0) {
   const size_t need = (size_t)c->N * Wv;
   if (need > c->vec_cap) {
     const size_t cap = need + need / 4 + 1024;
@@ -629,6 +650,11 @@ int ensure_vec(hk_ctx *c, int Wv, int Cs, int rows) {
     CK(alloc(c, c->sol_arena, &c->vecAsign, (size_t)c->N));
     CK(alloc(c, c->sol_arena, &c->vecBsign, (size_t)c->N));
     c->vec_cap = cap;
+  }
+  if (kar_stride > 0 && (size_t)c->N * kar_stride > c->vecAexp_cap) {
+    const size_t cap = (size_t)c->N * kar_stride;
+    CK(alloc(c, c->sol_arena, &c->vecAexp, cap));
+    c->vecAexp_cap = cap;
   }
   const size_t cneed = (size_t)rows * Cs;
   if (cneed > c->colsum_s_cap) {
@@ -706,17 +732,24 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
         top = 4 * 32;
       }
       sp.nosum = have_known ? 0 : 1;
-      const int Wv = std::max(4, round4((top - h + 31) / 32));
+      // Karatsuba on the factor's split points when the vector fits the
+      // factor's window W: the solve contracts expanded entries like the factor
+      const int Wv_need = std::max(4, round4((top - h + 31) / 32));
+      const int lv = c->fac_levels > 0 && c->Aexp && c->update_path == 0 && Wv_need <= W ? c->fac_levels : 0;
+      const int Wv = lv > 0 ? W : Wv_need;
       if (have_known) {
         c->wv_max = std::max<long long>(c->wv_max, Wv);
         c->wv_sum += Wv;
         c->wv_count++;
       }
       Sched sc;
-      CK(sched_for(c, W, Wv, 0, &sc));
+      CK(sched_for(c, W, Wv, lv, &sc));
       const int Cs = sc.C;
-      int rc = ensure_vec(c, Wv, Cs, nbs);
+      int rc = ensure_vec(c, Wv, Cs, nbs, lv > 0 ? c->kl.stride : 0);
       if (rc) return rc;
+      sp.kl = c->kl;
+      if (lv == 0) sp.kl.levels = 0;
+      sp.vecAexp = c->vecAexp;
       sp.vecA = c->vecA;
       sp.vecAsign = c->vecAsign;
       sp.Wv = Wv;
@@ -733,23 +766,28 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
                             (long long)c->vec_cap, c->stream));
         DBG(c, "solve vec_align", B0, Wv);
         c->launches++;
+        if (lv > 0) {
+          CK(launch_vec_expand(k0, k1, c->vecA, c->kl, c->vecAexp, c->stream));
+          DBG(c, "solve vec_expand", B0, Wv);
+          c->launches++;
+        }
       }
       UpdParams up;
       std::memset(&up, 0, sizeof(up));
       up.mode = back ? M_GEMV_BACK : M_GEMV_FWD;
       up.N = N;
-      up.A = c->A;
+      up.A = lv > 0 ? c->Aexp : c->A;
       up.Asign = c->Asign;
-      up.astride = W;
-      up.Vy = c->vecA;
+      up.astride = lv > 0 ? c->kl.stride : W;
+      up.Vy = lv > 0 ? c->vecAexp : c->vecA;
       up.Vysign = c->vecAsign;
-      up.vstride = Wv;
-      up.cx = W;
-      up.cy = Wv;
+      up.vstride = lv > 0 ? c->kl.stride : Wv;
+      up.cx = up.astride;
+      up.cy = up.vstride;
       up.r0 = B0;
       up.colsum = c->colsum_s;
-      up.a_len = c->A_len;
-      up.vy_len = (long long)c->vec_cap;
+      up.a_len = lv > 0 ? c->Aexp_len : c->A_len;
+      up.vy_len = lv > 0 ? (long long)c->vecAexp_cap : (long long)c->vec_cap;
       up.colsum_len = (long long)c->colsum_s_cap;
       fill_sched(up, sc);
       up.st = c->st;
@@ -767,7 +805,17 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
         c->launches++;
       }
       sp.h = h;
-      for (int s = 0; s < B1 - B0; s++) {
+      // low precision: the whole block in one launch (its per-row launches
+      // would cost more than their work); high precision: entry by entry with
+      // many-CTA in-block updates
+      const bool fused = (long long)W * Wv <= c->fuse_ww && Cs >= W + Wv + 4 &&
+                         solve_block_smem(L, Cs, W, Wv, B1 - B0) <= 160 * 1024;
+      if (fused) {
+        CK(launch_solve_block(sp, c->A, c->Asign, B0, B1, c->stream));
+        DBG(c, "solve block", B0, Wv);
+        c->launches++;
+      }
+      for (int s = 0; s < B1 - B0 && !fused; s++) {
         const int i = back ? B1 - 1 - s : B0 + s;
         // the first entry of each solve has no sum: the kernel takes G from the rhs
         CK(launch_solve_entry(sp, i, c->stream));
@@ -1040,6 +1088,7 @@ int hk_load_moments_flat(hk_ctx *c, int N, int bnum, int bden, int P, const int3
     c->sol_ready = false;
     c->hist_cap = 0;
     c->vec_cap = 0;
+    c->vecAexp_cap = 0;
     c->colsum_s_cap = 0;
     c->fac_N = c->fac_L = c->fac_W = 0;
     c->mom = MpArr{};
@@ -1115,7 +1164,11 @@ int hk_factor(hk_ctx *c, int *bad_row) {
     // a window failure invalidates everything after it (including a later
     // pivot test): widen the window below and above, and start again
     if (st.range_fail) {
-      const long long delta = (st.need_bits + 64 + 31) / 32 * 32;
+      // the sequence stops at the first failing launch, so the shortfall seen
+      // is a lower bound for the rows after it: widen generously (twice the
+      // shortfall, at least N/2 bits) so that one restart usually suffices
+      const long long want = std::max(2 * st.need_bits, (long long)c->N / 2) + 64;
+      const long long delta = (want + 31) / 32 * 32;
       c->top_margin += delta;
       c->W = round4(c->W + 2 * delta / 32);
       c->widenings++;
@@ -1222,6 +1275,7 @@ int hk_smallest_eig(hk_ctx *c, int iters, hk_mp *lambda_min, int *iters_used) {
   if (!c->factored) return HK_ERR_STATE;
   cudaSetDevice(c->device);
   const int T = iters > 0 ? iters : c->max_iters;
+  if (const char *e = getenv("HK_FUSE_WW")) c->fuse_ww = atoll(e);  // (tuning and tests)
   c->eig_converged = 0;
   c->wv_max = c->wv_sum = c->wv_count = 0;
   int rc = ensure_solve_buffers(c, T);

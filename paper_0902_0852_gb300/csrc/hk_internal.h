@@ -22,6 +22,7 @@ constexpr int UNT = 256;       // compute threads per CTA
 constexpr int USTAGES = 4;     // shared-memory pipeline depth
 constexpr int MAX_SUB = 9;     // sub-contractions per launch (two Karatsuba levels)
 constexpr int MAX_TERMS = 4;   // result positions a sub-contraction is added to
+constexpr int MAX_XB = 64;     // blocks per output with their own operand window
 
 struct Unit {
   int d0;  // first column of the stripe, sub-contraction index in bits 24..31
@@ -82,12 +83,23 @@ struct UpdParams {
   const Unit *units;
   int nunits;
   DevStatus *st;
+  // Per-block operand windows (Karatsuba launches): block x stages only limbs
+  // [xlo[x], xlo[x] + xlen[x]) of each expanded entry -- the pieces its units
+  // read plus one zero gap on each side.  nxb = 0: whole entries (cx, cy).
+  int nxb;
+  int xlo[MAX_XB], xlen[MAX_XB];
 };
 
 // Host-side schedule helpers.
 void kar_layout(int W, int levels, int gap, KarLayout *kl);
 int kar_subprobs(const KarLayout &kl, SubProb *sub);   // returns the count
 int build_units(const SubProb *sub, int nsub, int uc, int upc, Unit *host_out, int cap);
+// Operand windows of the blocks of a Karatsuba launch (pieces separated by
+// zero gaps of `gap` limbs inside entries of `stride` limbs): fills xlo/xlen
+// for the (n + 255) / 256 blocks and returns the longest window, or 0 when the
+// launch has one sub-problem or too many blocks (whole entries are staged).
+int operand_windows(const SubProb *sub, int nsub, const Unit *units, int n, int gap, int stride, int *xlo,
+                    int *xlen);
 void choose_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc, int *upc);
 int colsum_width(const SubProb *sub, int nsub, int uc);
 cudaError_t launch_update(const UpdParams &p, cudaStream_t s);
@@ -135,8 +147,15 @@ struct SolveParams {
   int nosum;               // first entry of a solve: no sum, no aligned copy
   DevStatus *st;
   long long vec_len, colsum_len;  // buffer sizes, for checked builds
+  KarLayout kl;            // levels > 0: also write the Karatsuba expansion of the aligned copy
+  uint32_t *vecAexp;       // [N][kl.stride] expanded aligned entries (Wv = kl.W)
 };
 cudaError_t launch_solve_entry(const SolveParams &p, int i, cudaStream_t s);
+// All rows [B0, B1) of a solve block in one single-CTA launch, in-block terms
+// from the plain aligned entries A (W limbs) and their signs (low precision).
+cudaError_t launch_solve_block(const SolveParams &p, const uint32_t *A, const int32_t *Asign, int B0, int B1,
+                               cudaStream_t s);
+size_t solve_block_smem(int L, int C, int W, int Wv, int nb);
 cudaError_t launch_vec_exprange(int n, MpArr v, int L, const long long *colU, int scaled,
                                 long long *out2, cudaStream_t s);
 cudaError_t launch_vec_align(int n0, int n1, MpArr v, int L, const long long *colU, int scaled,
@@ -145,6 +164,10 @@ cudaError_t launch_vec_align(int n0, int n1, MpArr v, int L, const long long *co
 cudaError_t launch_lambda(int L, const long long *colsum, int C, long long hv, long long hw,
                           MpArr lam, int slot, DevStatus *st, long long colsum_len, cudaStream_t s);
 cudaError_t launch_vec_normalise(int n, MpArr w, MpArr v, int L, cudaStream_t s);
+// Karatsuba expansion of aligned vector entries [n0, n1) (kl.W limbs each) into
+// dst (kl.stride limbs each).
+cudaError_t launch_vec_expand(int n0, int n1, const uint32_t *vecA, const KarLayout &kl, uint32_t *dst,
+                              cudaStream_t s);
 cudaError_t launch_set_ones(int n, MpArr v, int L, cudaStream_t s);
 
 // ---- self test (hk_selftest.cu) ---------------------------------------------------

@@ -10,6 +10,7 @@
 // The sums arrive exactly as column sums from the update kernel (modes
 // GEMV_FWD / GEMV_BACK / DOT) on a binary grid chosen by the host.
 #include "hk_internal.h"
+#include "hk_kar.cuh"
 #include "hk_mp.cuh"
 
 namespace hk {
@@ -131,6 +132,8 @@ __global__ void __launch_bounds__(NT_SOLVE) k_solve_entry(SolveParams p, int i) 
     for (int l = threadIdx.x; l < L; l += NT_SOLVE) outl[l] = 0;
     if (!p.nosum)
       for (int l = threadIdx.x; l < p.Wv; l += NT_SOLVE) va[l] = 0;
+    if (!p.nosum && p.kl.levels > 0)
+      for (int l = threadIdx.x; l < p.kl.stride; l += NT_SOLVE) p.vecAexp[(long long)i * p.kl.stride + l] = 0;
     if (threadIdx.x == 0) {
       p.out.sign[i] = 0;
       p.out.exp[i] = 0;
@@ -162,6 +165,182 @@ __global__ void __launch_bounds__(NT_SOLVE) k_solve_entry(SolveParams p, int i) 
     return;
   }
   mp::shl<NT_SOLVE>(s.res, L, sh, va, p.Wv);
+  if (p.kl.levels > 0) {
+    __syncthreads();
+    expand_entry<NT_SOLVE>(va, p.kl, p.vecAexp + (long long)i * p.kl.stride, s.cs, s.Z, s.big, *s.red);
+  }
+}
+
+// A whole block of solve rows in one launch (low precision, where the per-row
+// launches dominate): rows [B0, B1) in solve order, each
+//   out_i = RNE(RNE(rhs_i - colsum_i - sum_{k earlier in the block} R.. y_k) / R_ii)
+// with colsum_i the exact sum over the earlier blocks (one GEMV launch) and the
+// in-block terms computed here, exactly, from the block's aligned entries kept
+// in shared memory.  Same arithmetic as k_solve_entry + the in-block updates.
+struct BlockSmem {
+  uint32_t *Ys, *Xs;        // aligned in-block entries [nb][Wv]; staged R entries [nb][W]
+  int *Ysg, *Xsg;           // their signs
+  long long *cs2;           // in-block column sums [W + Wv + 4]
+};
+
+__host__ __device__ inline size_t block_smem_size(int L, int C, int W, int Wv, int nb, BlockSmem *out,
+                                                  unsigned char *base) {
+  size_t off = (scarve(nullptr, L, C, false, nullptr) + 15) / 16 * 16;
+  auto at = [&](size_t bytes) {
+    unsigned char *r = base ? base + off : nullptr;
+    off += (bytes + 15) / 16 * 16;
+    return r;
+  };
+  BlockSmem b;
+  b.Ys = reinterpret_cast<uint32_t *>(at(4 * (size_t)nb * Wv));
+  b.Xs = reinterpret_cast<uint32_t *>(at(4 * (size_t)nb * W));
+  b.Ysg = reinterpret_cast<int *>(at(4 * (size_t)nb));
+  b.Xsg = reinterpret_cast<int *>(at(4 * (size_t)nb));
+  b.cs2 = reinterpret_cast<long long *>(at(8 * (size_t)(W + Wv + 4)));
+  if (out) *out = b;
+  return off;
+}
+
+__global__ void __launch_bounds__(NT_SOLVE) k_solve_block(SolveParams p, const uint32_t *A, const int32_t *Asign,
+                                                          int B0, int B1) {
+  if (block_status(p.st) != ST_OK) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = p.L, N = p.N, W = p.W, Wv = p.Wv, nb = B1 - B0;
+  if (!HK_CHECK(p.st, block_smem_size(L, p.C, W, Wv, nb, nullptr, nullptr) <= dynamic_smem_bytes(), 24,
+                block_smem_size(L, p.C, W, Wv, nb, nullptr, nullptr), dynamic_smem_bytes()) ||
+      !HK_CHECK(p.st, (long long)nb * p.C <= p.colsum_len && p.C >= W + Wv + 4, 25, (long long)nb * p.C,
+                p.colsum_len))
+    return;
+  SSmem s;
+  scarve(smem_raw, L, p.C, false, &s);
+  BlockSmem b;
+  block_smem_size(L, p.C, W, Wv, nb, &b, smem_raw);
+  mp::Work w = swork(s);
+  const long long P = 32LL * L;
+  const int ncol = W + Wv + 2;
+  for (int step = 0; step < nb; step++) {
+    const int i = p.back ? B1 - 1 - step : B0 + step;
+    // in-block terms: sum over the earlier entries k of this block of R y_k
+    // (forward: R_ki on column i's grid; back: R_ik on column k's grid, with
+    // y_k scaled by 2^g_k), exact, as column sums on the row's grid
+    for (int d = threadIdx.x; d < ncol + 2; d += NT_SOLVE) b.cs2[d] = 0;
+    for (int q = 0; q < step; q++) {
+      const int k = p.back ? B1 - 1 - q : B0 + q;
+      const long long aidx = p.back ? tri_idx(i, k, N) : tri_idx(k, i, N);
+      for (int l = threadIdx.x; l < W; l += NT_SOLVE) b.Xs[q * W + l] = A[aidx * W + l];
+      if (threadIdx.x == 0) b.Xsg[q] = Asign[aidx] ^ b.Ysg[q];
+    }
+    __syncthreads();
+    if (step > 0) {
+      unsigned long long *cu = reinterpret_cast<unsigned long long *>(b.cs2);
+      for (int d = threadIdx.x; d < W + Wv - 1; d += NT_SOLVE) {
+        uint32_t p0 = 0, p1 = 0, p2 = 0, n0 = 0, n1 = 0, n2 = 0;
+        const int plo = max(0, d - Wv + 1), phi = min(W - 1, d);
+        for (int q = 0; q < step; q++) {
+          const uint32_t *X = b.Xs + q * W, *Y = b.Ys + q * Wv;
+          if (b.Xsg[q]) {
+            for (int pp = plo; pp <= phi; pp++) mp::mac3(n0, n1, n2, X[pp], Y[d - pp]);
+          } else {
+            for (int pp = plo; pp <= phi; pp++) mp::mac3(p0, p1, p2, X[pp], Y[d - pp]);
+          }
+        }
+        // positive minus negative words, added at columns d, d+1, d+2
+        const long long v0 = (long long)p0 - (long long)n0, v1 = (long long)p1 - (long long)n1,
+                        v2 = (long long)p2 - (long long)n2;
+        if (v0) atomicAdd(cu + d, (unsigned long long)v0);
+        if (v1) atomicAdd(cu + d + 1, (unsigned long long)v1);
+        if (v2) atomicAdd(cu + d + 2, (unsigned long long)v2);
+      }
+      __syncthreads();
+    }
+    // the entry itself (as k_solve_entry, with the in-block sums added)
+    const long long gi = p.colU[i] - 32LL * W;
+    long long G = p.back ? p.h : gi + p.h;
+    if (p.nosum) G = p.rhs.exp[i];
+    const long long *colrow = p.colsum + (long long)(i - p.r0) * p.C;
+    const uint32_t *vl = p.rhs.limbs + (long long)i * L;
+    bool vz = true;
+    for (int l = 0; l < L; l++) vz &= (vl[l] == 0);
+    long long sh0 = p.rhs.exp[i] - G;
+    if (vz) sh0 = 0;
+    if (sh0 < 0) {
+      if (threadIdx.x == 0) raise_range(p.st, -sh0);
+      return;
+    }
+    const long long q0 = sh0 >> 5;
+    const int b0 = (int)(sh0 & 31);
+    const int nm = vz ? 0 : (int)(q0 + L + 1);
+    const int nZ0 = max(p.C, nm);
+    if (nZ0 + 2 > s.cap) {
+      if (threadIdx.x == 0) raise_range(p.st, 32LL * (nZ0 + 2 - s.cap));
+      return;
+    }
+    const int32_t sv = p.rhs.sign[i];
+    for (int d = threadIdx.x; d < nZ0; d += NT_SOLVE) {
+      uint32_t mv = 0;
+      if (!vz) {
+        const long long li = d - q0;
+        const uint32_t a = mp::limb_at(vl, L, li), c = mp::limb_at(vl, L, li - 1);
+        mv = b0 ? ((a << b0) | (c >> (32 - b0))) : a;
+      }
+      const long long cv = (d < p.C ? colrow[d] : 0) + (d < ncol + 2 ? b.cs2[d] : 0);
+      s.cs[d] = (sv ? -(long long)mv : (long long)mv) - cv;
+    }
+    __syncthreads();
+    const bool neg = mp::resolve<NT_SOLVE>(s.cs, nZ0, s.Z, *s.red);
+    const int sgn = neg ? -1 : 1;
+    const mp::Rounded S = mp::round_rne<NT_SOLVE>(s.Z, nZ0 + 2, G, L, s.mant, w);
+    uint32_t *outl = p.out.limbs + (long long)i * L;
+    uint32_t *ya = b.Ys + step * Wv;
+    if (!S.nonzero) {
+      for (int l = threadIdx.x; l < L; l += NT_SOLVE) outl[l] = 0;
+      for (int l = threadIdx.x; l < Wv; l += NT_SOLVE) ya[l] = 0;
+      if (threadIdx.x == 0) {
+        p.out.sign[i] = 0;
+        p.out.exp[i] = 0;
+        b.Ysg[step] = 0;
+      }
+      __syncthreads();
+      continue;
+    }
+    const long long iidx = tri_idx(i, i, N);
+    for (int l = threadIdx.x; l < L; l += NT_SOLVE) s.rm[l] = p.R.limbs[iidx * L + l];
+    for (int l = threadIdx.x; l < L + 2; l += NT_SOLVE) s.V[l] = p.recip[(long long)i * (L + 2) + l];
+    __syncthreads();
+    bool ok = true;
+    const mp::Rounded Q =
+        mp::div_rne<NT_SOLVE>(s.mant, S.exp, s.rm, p.R.exp[iidx], s.V, L, s.res, w, s.big, s.q, &ok);
+    for (int l = threadIdx.x; l < L; l += NT_SOLVE) outl[l] = s.res[l];
+    if (threadIdx.x == 0) {
+      p.out.sign[i] = sgn < 0 ? 1 : 0;
+      p.out.exp[i] = Q.exp;
+      b.Ysg[step] = sgn < 0 ? 1 : 0;
+      if (!ok) atomicAdd(&p.st->timeout, 1);
+    }
+    // aligned copy (shared memory only: later blocks re-align from `out`)
+    if (step + 1 < nb && !p.nosum) {
+      const long long sh = Q.exp + (p.back ? gi : 0) - p.h;
+      if (sh < 0 || sh + P > 32LL * Wv) {
+        if (threadIdx.x == 0) raise_range(p.st, sh < 0 ? -sh : sh + P - 32LL * Wv);
+        return;
+      }
+      mp::shl<NT_SOLVE>(s.res, L, sh, ya, Wv);
+    }
+    __syncthreads();
+  }
+}
+
+// Karatsuba expansion of aligned vector entries (one block per entry)
+constexpr int NT_EXP = 128;
+__global__ void __launch_bounds__(NT_EXP) k_vec_expand(int n0, const uint32_t *vecA, KarLayout kl, uint32_t *dst) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int k = n0 + blockIdx.x;
+  const int h1 = kl.W / 2 + 8;  // level-1 sum width + normalize room
+  mp::Red *red = reinterpret_cast<mp::Red *>(smem_raw);
+  long long *cs = reinterpret_cast<long long *>(smem_raw + ((sizeof(mp::Red) + 15) / 16) * 16);
+  uint32_t *t1 = reinterpret_cast<uint32_t *>(cs + h1);
+  uint32_t *t2 = t1 + h1;
+  expand_entry<NT_EXP>(vecA + (long long)k * kl.W, kl, dst + (long long)k * kl.stride, cs, t1, t2, *red);
 }
 
 // min lsb exponent and max top exponent over the nonzero entries [0, n)
@@ -327,6 +506,19 @@ cudaError_t launch_solve_entry(const SolveParams &p, int i, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+size_t solve_block_smem(int L, int C, int W, int Wv, int nb) {
+  return block_smem_size(L, C, W, Wv, nb, nullptr, nullptr);
+}
+
+cudaError_t launch_solve_block(const SolveParams &p, const uint32_t *A, const int32_t *Asign, int B0, int B1,
+                               cudaStream_t s) {
+  const size_t smem = block_smem_size(p.L, p.C, p.W, p.Wv, B1 - B0, nullptr, nullptr);
+  cudaError_t e = set_smem((const void *)k_solve_block, smem);
+  if (e != cudaSuccess) return e;
+  k_solve_block<<<1, NT_SOLVE, smem, s>>>(p, A, Asign, B0, B1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_vec_exprange(int n, MpArr v, int L, const long long *off, int scaled, long long *out2,
                                 cudaStream_t s) {
   k_vec_exprange<<<1, 256, 0, s>>>(n, v, L, scaled ? off : nullptr, out2);
@@ -352,6 +544,17 @@ cudaError_t launch_lambda(int L, const long long *colsum, int C, long long hv, l
 
 cudaError_t launch_vec_normalise(int n, MpArr w, MpArr v, int L, cudaStream_t s) {
   k_vec_normalise<<<1, 1024, 0, s>>>(n, w, v, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vec_expand(int n0, int n1, const uint32_t *vecA, const KarLayout &kl, uint32_t *dst,
+                              cudaStream_t s) {
+  if (n1 <= n0) return cudaSuccess;
+  const int h1 = kl.W / 2 + 8;
+  const size_t smem = ((sizeof(mp::Red) + 15) / 16) * 16 + (size_t)h1 * 8 + (size_t)h1 * 4 * 2;
+  cudaError_t e = set_smem((const void *)k_vec_expand, smem);
+  if (e != cudaSuccess) return e;
+  k_vec_expand<<<n1 - n0, NT_EXP, smem, s>>>(n0, vecA, kl, dst);
   return cudaGetLastError();
 }
 

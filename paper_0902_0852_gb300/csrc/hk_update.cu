@@ -153,7 +153,7 @@ HK_DEV void decode_output(const UpdParams &p, int o, int *oi, int *oj, long long
 }
 
 #ifndef HK_UPDATE_MINBLOCKS
-#define HK_UPDATE_MINBLOCKS 2
+#define HK_UPDATE_MINBLOCKS 3
 #endif
 template <int UC>
 __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const __grid_constant__ UpdParams p) {
@@ -204,7 +204,10 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t bytesX = (uint32_t)p.cx * 4u, bytesY = (uint32_t)p.cy * 4u;
+  // operand window of this block (whole entries when nxb = 0)
+  const int wlo = p.nxb ? p.xlo[blockIdx.x] : 0;
+  const uint32_t bytesX = (uint32_t)(p.nxb ? p.xlen[blockIdx.x] : p.cx) * 4u;
+  const uint32_t bytesY = (uint32_t)(p.nxb ? p.xlen[blockIdx.x] : p.cy) * 4u;
 
   if (warp == UNT / 32) {
     // ---------------- producer warp ----------------
@@ -227,12 +230,13 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
           const long long lx = p.mode == M_DOT ? p.vx_len : p.a_len;
           const uint32_t *by = p.mode == M_FACTOR ? p.A : (p.mode == M_DOT && oj == 0 ? p.Vx : p.Vy);
           const long long ly = p.mode == M_FACTOR ? p.a_len : (p.mode == M_DOT && oj == 0 ? p.vx_len : p.vy_len);
-          const long long ox = op.x - bx, oy = op.y - by;
-          if (!HK_CHECK(p.st, ox >= 0 && ox + p.cx <= lx, 2, ox, lx) ||
-              !HK_CHECK(p.st, oy >= 0 && oy + p.cy <= ly, 3, oy, ly) ||
-              !HK_CHECK(p.st, ((uintptr_t)op.x & 15) == 0 && ((uintptr_t)op.y & 15) == 0 && (bytesX & 15) == 0 &&
-                                  (bytesY & 15) == 0,
-                        4, (long long)((uintptr_t)op.x & 15), (long long)((uintptr_t)op.y & 15))) {
+          const long long ox = op.x + wlo - bx, oy = op.y + wlo - by;
+          if (!HK_CHECK(p.st, ox >= 0 && ox + bytesX / 4 <= lx, 2, ox, lx) ||
+              !HK_CHECK(p.st, oy >= 0 && oy + bytesY / 4 <= ly, 3, oy, ly) ||
+              !HK_CHECK(p.st, ((uintptr_t)(op.x + wlo) & 15) == 0 && ((uintptr_t)(op.y + wlo) & 15) == 0 &&
+                                  (bytesX & 15) == 0 && (bytesY & 15) == 0 && bytesX <= 4u * p.cx &&
+                                  bytesY <= 4u * p.cy,
+                        4, (long long)((uintptr_t)(op.x + wlo) & 15), (long long)bytesX)) {
             *abort_flag = 1;
             break;
           }
@@ -242,8 +246,8 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
         uint32_t *ys = xs + Xsz + YPADL;
         sneg[s] = op.neg;
         mbar_expect_tx(&full[s], bytesX + bytesY);
-        bulk_g2s(xs, op.x, bytesX, &full[s]);
-        bulk_g2s(ys, op.y, bytesY, &full[s]);
+        bulk_g2s(xs, op.x + wlo, bytesX, &full[s]);
+        bulk_g2s(ys, op.y + wlo, bytesY, &full[s]);
         issued = it + 1;
       }
       if (*abort_flag) {
@@ -264,14 +268,17 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
   // a unit table entry must name one of this launch's sub-problems (always
   // checked: a bad entry would index the operand tiles with wrong offsets)
   if (active && sp >= p.nsub) active = check_fail(p.st, 5, sp, p.nsub);
-  const int xoff = p.sub[active ? sp : 0].xoff, yoff = p.sub[active ? sp : 0].yoff;
+  const int xoff = p.sub[active ? sp : 0].xoff - wlo, yoff = p.sub[active ? sp : 0].yoff - wlo;
 #ifdef HK_CHECKED
   if (active) {
     // every shared-memory word the unit reads lies in its stage's X or Y tile
+    // (inside the block's operand window when it has one)
+    const long long xlim = p.nxb ? p.xlen[blockIdx.x] : Xsz;
+    const long long ymin = p.nxb ? YPADL : 0, ylim = p.nxb ? YPADL + p.xlen[blockIdx.x] : Ysz;
     const long long xlo = xoff + p0, xhi = xoff + p0 + p.upc - 1;
     const long long ylo = YPADL + yoff + d0 - p0 - p.upc + 1, yhi = YPADL + yoff + d0 - p0 + UC - 1;
-    if (!HK_CHECK(p.st, xlo >= 0 && xhi < Xsz, 6, xhi, Xsz) ||
-        !HK_CHECK(p.st, ylo >= 0 && yhi < Ysz, 7, ylo < 0 ? ylo : yhi, Ysz) ||
+    if (!HK_CHECK(p.st, xlo >= 0 && xhi < xlim, 6, xhi, xlim) ||
+        !HK_CHECK(p.st, ylo >= ymin && yhi < ylim, 7, ylo < ymin ? ylo : yhi, ylim) ||
         !HK_CHECK(p.st, crow * p.C + p.C <= p.colsum_len, 8, crow * p.C + p.C, p.colsum_len))
       active = false;
   }
@@ -511,6 +518,27 @@ int build_units(const SubProb *sub, int nsub, int uc, int upc, Unit *out, int ca
         }
   }
   return n;
+}
+
+int operand_windows(const SubProb *sub, int nsub, const Unit *units, int n, int gap, int stride, int *xlo,
+                    int *xlen) {
+  const int nb = (n + UNT - 1) / UNT;
+  if (nsub <= 1 || nb > MAX_XB || n <= 0) return 0;
+  int maxlen = 0;
+  for (int b = 0; b < nb; b++) {
+    int lo = INT_MAX, hi = 0;
+    for (int u = b * UNT; u < std::min(n, (b + 1) * UNT); u++) {
+      const int q = (units[u].d0 >> 24) & 0xff;
+      lo = std::min(lo, sub[q].xoff - gap);
+      hi = std::max(hi, sub[q].xoff + ((sub[q].wx + 3) / 4) * 4 + gap);
+    }
+    lo = std::max(0, lo & ~3);
+    hi = std::min(stride, (hi + 3) & ~3);
+    xlo[b] = lo;
+    xlen[b] = hi - lo;
+    maxlen = std::max(maxlen, hi - lo);
+  }
+  return maxlen;
 }
 
 // Schedule: stripe width and chunk length (a multiple of it, at most upc_cap)

@@ -223,21 +223,24 @@ def features(N, beta):
 
 
 def encode_targets(N, bits, log2_lambda, iters):
-    """Network outputs: required bits per row, log2 lambda_min per sqrt(N),
-    log2 of the iteration count."""
-    return [bits / N, log2_lambda / math.sqrt(N), math.log2(max(iters, 1))]
+    """Network outputs: required bits above the 128-bit accuracy target per
+    row, log2 lambda_min per row, log2 of the iteration count.  The method's
+    data make the first two nearly independent of N for a fixed beta (the
+    requirement grows linearly in N), so the network extrapolates in N
+    without bending."""
+    return [(bits - AGREE_BITS) / N, log2_lambda / N, math.log2(max(iters, 1))]
 
 
 def decode_targets(N, y):
-    return y[0] * N, y[1] * math.sqrt(N), 2.0 ** y[2]
+    return y[0] * N + AGREE_BITS, y[1] * N, 2.0 ** y[2]
 
 
 class Predictor:
     """The 2 -> 64 -> 64 -> 3 network on the device, with the scalings above
     and standardisation of features and targets."""
 
-    def __init__(self, params=None, x_mean=None, x_std=None, y_mean=None, y_std=None, margin_bits=64,
-                 iter_factor=1.5, device=0):
+    def __init__(self, params=None, x_mean=None, x_std=None, y_mean=None, y_std=None, margin_bits=32,
+                 iter_factor=1.5, device=0, margin_per_row=0.0):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", device)
@@ -250,6 +253,7 @@ class Predictor:
         self.y_mean = np.zeros(3) if y_mean is None else np.asarray(y_mean, dtype=np.float64)
         self.y_std = np.ones(3) if y_std is None else np.asarray(y_std, dtype=np.float64)
         self.margin_bits = margin_bits
+        self.margin_per_row = margin_per_row
         self.iter_factor = iter_factor
 
     @staticmethod
@@ -290,12 +294,15 @@ class Predictor:
             done += n
         torch.cuda.synchronize()
         h = hist.cpu().numpy()
-        # margin: cover the largest under-prediction of the training set
+        # margin: 32 bits plus, per row, the largest relative under-prediction
+        # of the training set (errors grow with N like the requirement itself)
         pred = self.predict_raw([(t["N"], tuple(t["beta"])) for t in rows])
-        under = [t["bits"] - b for t, (b, _, _) in zip(rows, pred)]
-        self.margin_bits = int(max(32, _ceil32(max(under) + 16)))
+        under = [(t["bits"] - b) / t["N"] for t, (b, _, _) in zip(rows, pred)]
+        self.margin_bits = 32
+        self.margin_per_row = max(0.0, max(under))
         if log:
-            log(f"fit: {len(rows)} tuples, loss {h[0]:.4g} -> {h[-1]:.4g}, margin {self.margin_bits} bits")
+            log(f"fit: {len(rows)} tuples, loss {h[0]:.4g} -> {h[-1]:.4g}, margin 32 bits + "
+                f"{self.margin_per_row:.3f} bits per row")
         return h
 
     def predict_raw(self, rows):
@@ -310,7 +317,7 @@ class Predictor:
     def predict(self, N, beta):
         """(P, iteration budget, log2 lambda_min estimate) for one instance."""
         bits, l2, it = self.predict_raw([(N, beta)])[0]
-        P = max(P_MIN, _ceil32(bits + self.margin_bits))
+        P = max(P_MIN, _ceil32(bits + self.margin_bits + self.margin_per_row * N))
         P = min(P, p_conservative(N, beta))
         T = int(min(MAX_ITERS, max(8, math.ceil(it * self.iter_factor) + 4)))
         return P, T, l2
@@ -318,12 +325,13 @@ class Predictor:
     def to_json(self):
         return dict(params=[float(x) for x in self.params.cpu().numpy()], x_mean=list(self.x_mean),
                     x_std=list(self.x_std), y_mean=list(self.y_mean), y_std=list(self.y_std),
-                    margin_bits=self.margin_bits, iter_factor=self.iter_factor)
+                    margin_bits=self.margin_bits, margin_per_row=self.margin_per_row,
+                    iter_factor=self.iter_factor, targets="(bits-128)/N, log2(lambda)/N, log2(iters)")
 
     @classmethod
     def from_json(cls, d, device=0):
         return cls(d["params"], d["x_mean"], d["x_std"], d["y_mean"], d["y_std"], d["margin_bits"],
-                   d["iter_factor"], device)
+                   d["iter_factor"], device, d.get("margin_per_row", 0.0))
 
 
 # ----- verified solves ----------------------------------------------------------

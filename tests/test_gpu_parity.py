@@ -187,3 +187,17 @@ def test_int8_tensor_path_signed_entries(hk):
         h.factor()
         R = h.R()
     assert R == oracle.cholesky(mom, N, P)
+
+
+@pytest.mark.parametrize("fuse", ["0", "1000000000"])
+def test_solve_paths_bit_identical(hk, monkeypatch, fuse):
+    """Blocks solved entry by entry (many-CTA in-block updates) or in one
+    launch per block give the same history as the oracle (N = 40 crosses
+    three 16-row solve blocks)."""
+    monkeypatch.setenv("HK_FUSE_WW", fuse)
+    N, beta, P, T = 40, (7, 4), 384, 6
+    m, R, lam, hist, _ = gpu_run(hk, N, beta, P, T)
+    Ro = oracle.cholesky(m, N, P)
+    assert R == Ro
+    _, hist_o, _ = oracle.inverse_iteration(Ro, P, T)
+    assert hist == hist_o
