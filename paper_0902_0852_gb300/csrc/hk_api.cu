@@ -20,6 +20,7 @@ using namespace hk;
 
 // largest precision whose panel work areas fit in one block's shared memory
 static const int HK_MAX_P = 32768;
+static const int HK_MAX_WV = 12000;  // widest solve vector window (limbs) the update tiles can stage
 
 namespace {
 
@@ -133,11 +134,22 @@ int cuda_status(cudaError_t e) {
   return HK_ERR_CUDA;
 }
 
+#ifdef HK_CHECKED
+#define CK(x)                                                                                 \
+  do {                                                                                        \
+    cudaError_t e_ = (x);                                                                     \
+    if (e_ != cudaSuccess) {                                                                  \
+      fprintf(stderr, "[hk checked] %s:%d %s -> %s\n", __FILE__, __LINE__, #x, cudaGetErrorString(e_)); \
+      return cuda_status(e_);                                                                 \
+    }                                                                                         \
+  } while (0)
+#else
 #define CK(x)                                  \
   do {                                         \
     cudaError_t e_ = (x);                      \
     if (e_ != cudaSuccess) return cuda_status(e_); \
   } while (0)
+#endif
 
 #ifdef HK_CHECKED
 // Checked build: after every launch, wait for it and report a fault or a
@@ -735,8 +747,10 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
       // Karatsuba on the factor's split points when the vector fits the
       // factor's window W: the solve contracts expanded entries like the factor
       const int Wv_need = std::max(4, round4((top - h + 31) / 32));
-      const int lv = c->fac_levels > 0 && c->Aexp && c->update_path == 0 && Wv_need <= W ? c->fac_levels : 0;
+      const bool kar_ok = c->fac_levels > 0 && c->Aexp && c->update_path == 0;
+      const int lv = kar_ok && Wv_need <= W ? c->fac_levels : 0;
       const int Wv = lv > 0 ? W : Wv_need;
+      if (Wv > HK_MAX_WV) return HK_ERR_RANGE;  // no shared-memory tile could hold it
       if (have_known) {
         c->wv_max = std::max<long long>(c->wv_max, Wv);
         c->wv_sum += Wv;
@@ -848,7 +862,12 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
         CK(reset_status(c));
         continue;
       }
-      if (st.code != ST_OK) return st.code == ST_NOT_PD ? HK_ERR_NOT_PD : HK_ERR_CUDA;
+      if (st.code != ST_OK) {
+#ifdef HK_CHECKED
+        fprintf(stderr, "[hk checked] solve block %d status code %d check_site %d\n", B0, st.code, st.check_site);
+#endif
+        return st.code == ST_NOT_PD ? HK_ERR_NOT_PD : HK_ERR_CUDA;
+      }
       break;
     }
   }

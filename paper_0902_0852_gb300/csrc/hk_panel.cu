@@ -137,7 +137,8 @@ HK_DEV bool align_entry(const uint32_t *mant, int L, long long e, bool zero, lon
   return true;
 }
 
-__global__ void __launch_bounds__(NT_DIAG) k_diag(PanelParams p, int i) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_diag(PanelParams p, int i) {
   if (block_status(p.st) != ST_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RowSmem s;
@@ -158,10 +159,10 @@ __global__ void __launch_bounds__(NT_DIAG) k_diag(PanelParams p, int i) {
                 (tri_idx(i, i, N) + 1) * p.kl.stride, p.aexp_len))
     return;
   int nZ = 0;
-  const int sgn = form_exact<NT_DIAG>(s, colrow, p.C, p.mom.sign[mk], p.mom.exp[mk],
+  const int sgn = form_exact<NT>(s, colrow, p.C, p.mom.sign[mk], p.mom.exp[mk],
                                       p.mom.limbs + (long long)mk * L, L, 2 * gi, p.st, &nZ);
   if (sgn == 0) return;
-  const mp::Rounded S = mp::round_rne<NT_DIAG>(s.Z, nZ, 2 * gi, L, s.mant, w);
+  const mp::Rounded S = mp::round_rne<NT>(s.Z, nZ, 2 * gi, L, s.mant, w);
   if (!S.nonzero || sgn < 0) {
     if (threadIdx.x == 0) {
       atomicMin(&p.st->bad_row, i);
@@ -173,27 +174,28 @@ __global__ void __launch_bounds__(NT_DIAG) k_diag(PanelParams p, int i) {
   for (int t = 0; t < 6; t++) (&B.a)[t] = s.nb[t];
   B.cap = s.cap4;
   bool ok = true;
-  const mp::Rounded Rr = mp::sqrt_rne<NT_DIAG>(s.mant, L, S.exp, s.rm, w, B, s.big, s.xs, &ok);
+  const mp::Rounded Rr = mp::sqrt_rne<NT>(s.mant, L, S.exp, s.rm, w, B, s.big, s.xs, &ok);
   const long long idx = tri_idx(i, i, N);
-  for (int l = threadIdx.x; l < L; l += NT_DIAG) p.R.limbs[idx * L + l] = s.rm[l];
+  for (int l = threadIdx.x; l < L; l += NT) p.R.limbs[idx * L + l] = s.rm[l];
   if (threadIdx.x == 0) {
     p.R.sign[idx] = 0;
     p.R.exp[idx] = Rr.exp;
     p.Asign[idx] = 0;
     if (!ok) atomicAdd(&p.st->timeout, 1);
   }
-  align_entry<NT_DIAG>(s.rm, L, Rr.exp, false, gi, p.W, p.A + idx * p.W, p.st);
+  align_entry<NT>(s.rm, L, Rr.exp, false, gi, p.W, p.A + idx * p.W, p.st);
   __syncthreads();
   if (p.kl.levels > 0)
-    expand_entry<NT_DIAG>(p.A + idx * p.W, p.kl, p.Aexp + idx * p.kl.stride, s.cs, s.Z, s.big, *s.red);
+    expand_entry<NT>(p.A + idx * p.W, p.kl, p.Aexp + idx * p.kl.stride, s.cs, s.Z, s.big, *s.red);
   __syncthreads();
-  ok = mp::recip<NT_DIAG>(s.rm, L, s.V, w, B);
-  for (int l = threadIdx.x; l < L + 2; l += NT_DIAG) p.recip[(long long)i * (L + 2) + l] = s.V[l];
+  ok = mp::recip<NT>(s.rm, L, s.V, w, B);
+  for (int l = threadIdx.x; l < L + 2; l += NT) p.recip[(long long)i * (L + 2) + l] = s.V[l];
   if (threadIdx.x == 0 && !ok) atomicAdd(&p.st->timeout, 1);
   (void)P;
 }
 
-__global__ void __launch_bounds__(NT_ROW) k_offdiag(PanelParams p, int i) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_offdiag(PanelParams p, int i) {
   if (block_status(p.st) != ST_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RowSmem s;
@@ -216,17 +218,17 @@ __global__ void __launch_bounds__(NT_ROW) k_offdiag(PanelParams p, int i) {
                 (tri_idx(i, j, N) + 1) * p.kl.stride, p.aexp_len))
     return;
   int nZ = 0;
-  const int sgn = form_exact<NT_ROW>(s, colrow, p.C, p.mom.sign[mk], p.mom.exp[mk],
+  const int sgn = form_exact<NT>(s, colrow, p.C, p.mom.sign[mk], p.mom.exp[mk],
                                      p.mom.limbs + (long long)mk * L, L, gi + gj, p.st, &nZ);
   if (sgn == 0) return;
-  const mp::Rounded S = mp::round_rne<NT_ROW>(s.Z, nZ, gi + gj, L, s.mant, w);
+  const mp::Rounded S = mp::round_rne<NT>(s.Z, nZ, gi + gj, L, s.mant, w);
   const long long idx = tri_idx(i, j, N);
   const long long iidx = tri_idx(i, i, N);
   if (!S.nonzero) {
-    for (int l = threadIdx.x; l < L; l += NT_ROW) p.R.limbs[idx * L + l] = 0;
-    for (int l = threadIdx.x; l < p.W; l += NT_ROW) p.A[idx * p.W + l] = 0;
+    for (int l = threadIdx.x; l < L; l += NT) p.R.limbs[idx * L + l] = 0;
+    for (int l = threadIdx.x; l < p.W; l += NT) p.A[idx * p.W + l] = 0;
     if (p.kl.levels > 0)
-      for (int l = threadIdx.x; l < p.kl.stride; l += NT_ROW) p.Aexp[idx * p.kl.stride + l] = 0;
+      for (int l = threadIdx.x; l < p.kl.stride; l += NT) p.Aexp[idx * p.kl.stride + l] = 0;
     if (threadIdx.x == 0) {
       p.R.sign[idx] = 0;
       p.R.exp[idx] = 0;
@@ -234,21 +236,21 @@ __global__ void __launch_bounds__(NT_ROW) k_offdiag(PanelParams p, int i) {
     }
     return;
   }
-  for (int l = threadIdx.x; l < L; l += NT_ROW) s.rm[l] = p.R.limbs[iidx * L + l];
-  for (int l = threadIdx.x; l < L + 2; l += NT_ROW) s.V[l] = p.recip[(long long)i * (L + 2) + l];
+  for (int l = threadIdx.x; l < L; l += NT) s.rm[l] = p.R.limbs[iidx * L + l];
+  for (int l = threadIdx.x; l < L + 2; l += NT) s.V[l] = p.recip[(long long)i * (L + 2) + l];
   __syncthreads();
   bool ok = true;
-  const mp::Rounded Q = mp::div_rne<NT_ROW>(s.mant, S.exp, s.rm, p.R.exp[iidx], s.V, L, s.res, w, s.big, s.q, &ok);
-  for (int l = threadIdx.x; l < L; l += NT_ROW) p.R.limbs[idx * L + l] = s.res[l];
+  const mp::Rounded Q = mp::div_rne<NT>(s.mant, S.exp, s.rm, p.R.exp[iidx], s.V, L, s.res, w, s.big, s.q, &ok);
+  for (int l = threadIdx.x; l < L; l += NT) p.R.limbs[idx * L + l] = s.res[l];
   if (threadIdx.x == 0) {
     p.R.sign[idx] = sgn < 0 ? 1 : 0;
     p.R.exp[idx] = Q.exp;
     p.Asign[idx] = sgn < 0 ? 1 : 0;
     if (!ok) atomicAdd(&p.st->timeout, 1);
   }
-  if (align_entry<NT_ROW>(s.res, L, Q.exp, false, gj, p.W, p.A + idx * p.W, p.st) && p.kl.levels > 0) {
+  if (align_entry<NT>(s.res, L, Q.exp, false, gj, p.W, p.A + idx * p.W, p.st) && p.kl.levels > 0) {
     __syncthreads();
-    expand_entry<NT_ROW>(p.A + idx * p.W, p.kl, p.Aexp + idx * p.kl.stride, s.cs, s.Z, s.big, *s.red);
+    expand_entry<NT>(p.A + idx * p.W, p.kl, p.Aexp + idx * p.kl.stride, s.cs, s.Z, s.big, *s.red);
   }
 }
 
@@ -268,21 +270,40 @@ static cudaError_t set_smem(const void *fn, size_t bytes) {
   return bytes > 48 * 1024 ? allow_dynamic_smem(fn) : cudaSuccess;
 }
 
-cudaError_t launch_diag(const PanelParams &p, int i, cudaStream_t s) {
+// threads per CTA (templated for tuning; fewer threads measured slower)
+static int diag_threads(int L) {
+  (void)L;
+  return NT_DIAG;
+}
+
+template <int NT>
+static cudaError_t launch_diag_t(const PanelParams &p, int i, cudaStream_t s) {
   const size_t smem = panel_smem_diag(p.L, p.C);
-  cudaError_t e = set_smem((const void *)k_diag, smem);
+  cudaError_t e = set_smem((const void *)k_diag<NT>, smem);
   if (e != cudaSuccess) return e;
-  k_diag<<<1, NT_DIAG, smem, s>>>(p, i);
+  k_diag<NT><<<1, NT, smem, s>>>(p, i);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const PanelParams &p, int i, cudaStream_t s) {
+  switch (diag_threads(p.L)) {
+    case 256: return launch_diag_t<256>(p, i, s);
+    default: return launch_diag_t<NT_DIAG>(p, i, s);
+  }
+}
+
+template <int NT>
+static cudaError_t launch_offdiag_t(const PanelParams &p, int i, cudaStream_t s) {
+  const size_t smem = panel_smem_row(p.L, p.C);
+  cudaError_t e = set_smem((const void *)k_offdiag<NT>, smem);
+  if (e != cudaSuccess) return e;
+  k_offdiag<NT><<<p.N - i - 1, NT, smem, s>>>(p, i);
   return cudaGetLastError();
 }
 
 cudaError_t launch_offdiag(const PanelParams &p, int i, cudaStream_t s) {
   if (i + 1 >= p.N) return cudaSuccess;
-  const size_t smem = panel_smem_row(p.L, p.C);
-  cudaError_t e = set_smem((const void *)k_offdiag, smem);
-  if (e != cudaSuccess) return e;
-  k_offdiag<<<p.N - i - 1, NT_ROW, smem, s>>>(p, i);
-  return cudaGetLastError();
+  return launch_offdiag_t<NT_ROW>(p, i, s);
 }
 
 }  // namespace hk

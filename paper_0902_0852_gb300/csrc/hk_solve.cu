@@ -81,6 +81,16 @@ HK_DEV int form_exact_s(SSmem &s, const long long *colrow, int C, int32_t sv, lo
   }
   const long long q = sh >> 5;
   const int b = (int)(sh & 31);
+  if (!vz && q >= C + 2) {
+    // the sum (|sum| < 2^(32(C+1)), column sums below 2^63) lies more than 32
+    // bits below the lowest bit of the P-bit value v, i.e. under ulp(v)/2^32:
+    // RNE(v - sum) = v exactly.  Return v itself (no wide buffer needed).
+    for (int l = threadIdx.x; l < L; l += NT) s.Z[l] = vl[l];
+    for (int l = L + threadIdx.x; l < L + 2; l += NT) s.Z[l] = 0;
+    __syncthreads();
+    *nZ_out = -L;  // marker: s.Z holds v's mantissa, exponent ev
+    return sv ? -1 : 1;
+  }
   const int nm = vz ? 0 : (int)(q + L + 1);
   const int nZ = max(C, nm);
   if (nZ + 2 > s.cap) {
@@ -104,7 +114,8 @@ HK_DEV int form_exact_s(SSmem &s, const long long *colrow, int C, int32_t sv, lo
 }
 
 // one solve entry i: out_i = RNE(RNE(rhs_i - sum) / R_ii); aligned copy in vecA[i]
-__global__ void __launch_bounds__(NT_SOLVE) k_solve_entry(SolveParams p, int i) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_solve_entry(SolveParams p, int i) {
   if (block_status(p.st) != ST_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SSmem s;
@@ -122,18 +133,20 @@ __global__ void __launch_bounds__(NT_SOLVE) k_solve_entry(SolveParams p, int i) 
   if (p.nosum) G = p.rhs.exp[i];
   const long long *colrow = p.colsum + (long long)(i - p.r0) * p.C;
   int nZ = 0;
-  const int sgn = form_exact_s<NT_SOLVE>(s, colrow, p.C, p.rhs.sign[i], p.rhs.exp[i],
+  const int sgn = form_exact_s<NT>(s, colrow, p.C, p.rhs.sign[i], p.rhs.exp[i],
                                          p.rhs.limbs + (long long)i * L, L, G, p.st, &nZ);
   if (sgn == 0) return;
-  const mp::Rounded S = mp::round_rne<NT_SOLVE>(s.Z, nZ, G, L, s.mant, w);
+  // nZ < 0: the sum was negligible and s.Z holds the rhs mantissa itself
+  const mp::Rounded S = nZ < 0 ? mp::round_rne<NT>(s.Z, L, p.rhs.exp[i], L, s.mant, w)
+                               : mp::round_rne<NT>(s.Z, nZ, G, L, s.mant, w);
   uint32_t *outl = p.out.limbs + (long long)i * L;
   uint32_t *va = p.vecA + (long long)i * p.Wv;
   if (!S.nonzero) {
-    for (int l = threadIdx.x; l < L; l += NT_SOLVE) outl[l] = 0;
+    for (int l = threadIdx.x; l < L; l += NT) outl[l] = 0;
     if (!p.nosum)
-      for (int l = threadIdx.x; l < p.Wv; l += NT_SOLVE) va[l] = 0;
+      for (int l = threadIdx.x; l < p.Wv; l += NT) va[l] = 0;
     if (!p.nosum && p.kl.levels > 0)
-      for (int l = threadIdx.x; l < p.kl.stride; l += NT_SOLVE) p.vecAexp[(long long)i * p.kl.stride + l] = 0;
+      for (int l = threadIdx.x; l < p.kl.stride; l += NT) p.vecAexp[(long long)i * p.kl.stride + l] = 0;
     if (threadIdx.x == 0) {
       p.out.sign[i] = 0;
       p.out.exp[i] = 0;
@@ -142,13 +155,13 @@ __global__ void __launch_bounds__(NT_SOLVE) k_solve_entry(SolveParams p, int i) 
     return;
   }
   const long long iidx = tri_idx(i, i, N);
-  for (int l = threadIdx.x; l < L; l += NT_SOLVE) s.rm[l] = p.R.limbs[iidx * L + l];
-  for (int l = threadIdx.x; l < L + 2; l += NT_SOLVE) s.V[l] = p.recip[(long long)i * (L + 2) + l];
+  for (int l = threadIdx.x; l < L; l += NT) s.rm[l] = p.R.limbs[iidx * L + l];
+  for (int l = threadIdx.x; l < L + 2; l += NT) s.V[l] = p.recip[(long long)i * (L + 2) + l];
   __syncthreads();
   bool ok = true;
   const mp::Rounded Q =
-      mp::div_rne<NT_SOLVE>(s.mant, S.exp, s.rm, p.R.exp[iidx], s.V, L, s.res, w, s.big, s.q, &ok);
-  for (int l = threadIdx.x; l < L; l += NT_SOLVE) outl[l] = s.res[l];
+      mp::div_rne<NT>(s.mant, S.exp, s.rm, p.R.exp[iidx], s.V, L, s.res, w, s.big, s.q, &ok);
+  for (int l = threadIdx.x; l < L; l += NT) outl[l] = s.res[l];
   if (threadIdx.x == 0) {
     p.out.sign[i] = sgn < 0 ? 1 : 0;
     p.out.exp[i] = Q.exp;
@@ -164,10 +177,10 @@ __global__ void __launch_bounds__(NT_SOLVE) k_solve_entry(SolveParams p, int i) 
     if (threadIdx.x == 0) raise_range(p.st, sh < 0 ? -sh : sh + P - 32LL * p.Wv);
     return;
   }
-  mp::shl<NT_SOLVE>(s.res, L, sh, va, p.Wv);
+  mp::shl<NT>(s.res, L, sh, va, p.Wv);
   if (p.kl.levels > 0) {
     __syncthreads();
-    expand_entry<NT_SOLVE>(va, p.kl, p.vecAexp + (long long)i * p.kl.stride, s.cs, s.Z, s.big, *s.red);
+    expand_entry<NT>(va, p.kl, p.vecAexp + (long long)i * p.kl.stride, s.cs, s.Z, s.big, *s.red);
   }
 }
 
@@ -201,7 +214,8 @@ __host__ __device__ inline size_t block_smem_size(int L, int C, int W, int Wv, i
   return off;
 }
 
-__global__ void __launch_bounds__(NT_SOLVE) k_solve_block(SolveParams p, const uint32_t *A, const int32_t *Asign,
+template <int NT>
+__global__ void __launch_bounds__(NT) k_solve_block(SolveParams p, const uint32_t *A, const int32_t *Asign,
                                                           int B0, int B1) {
   if (block_status(p.st) != ST_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -223,17 +237,17 @@ __global__ void __launch_bounds__(NT_SOLVE) k_solve_block(SolveParams p, const u
     // in-block terms: sum over the earlier entries k of this block of R y_k
     // (forward: R_ki on column i's grid; back: R_ik on column k's grid, with
     // y_k scaled by 2^g_k), exact, as column sums on the row's grid
-    for (int d = threadIdx.x; d < ncol + 2; d += NT_SOLVE) b.cs2[d] = 0;
+    for (int d = threadIdx.x; d < ncol + 2; d += NT) b.cs2[d] = 0;
     for (int q = 0; q < step; q++) {
       const int k = p.back ? B1 - 1 - q : B0 + q;
       const long long aidx = p.back ? tri_idx(i, k, N) : tri_idx(k, i, N);
-      for (int l = threadIdx.x; l < W; l += NT_SOLVE) b.Xs[q * W + l] = A[aidx * W + l];
+      for (int l = threadIdx.x; l < W; l += NT) b.Xs[q * W + l] = A[aidx * W + l];
       if (threadIdx.x == 0) b.Xsg[q] = Asign[aidx] ^ b.Ysg[q];
     }
     __syncthreads();
     if (step > 0) {
       unsigned long long *cu = reinterpret_cast<unsigned long long *>(b.cs2);
-      for (int d = threadIdx.x; d < W + Wv - 1; d += NT_SOLVE) {
+      for (int d = threadIdx.x; d < W + Wv - 1; d += NT) {
         uint32_t p0 = 0, p1 = 0, p2 = 0, n0 = 0, n1 = 0, n2 = 0;
         const int plo = max(0, d - Wv + 1), phi = min(W - 1, d);
         for (int q = 0; q < step; q++) {
@@ -269,14 +283,19 @@ __global__ void __launch_bounds__(NT_SOLVE) k_solve_block(SolveParams p, const u
     }
     const long long q0 = sh0 >> 5;
     const int b0 = (int)(sh0 & 31);
+    const bool small_sum = !vz && q0 >= max(p.C, ncol + 2) + 2;  // RNE(v - sum) = v exactly
     const int nm = vz ? 0 : (int)(q0 + L + 1);
-    const int nZ0 = max(p.C, nm);
-    if (nZ0 + 2 > s.cap) {
+    const int nZ0 = small_sum ? L : max(p.C, nm);
+    if (!small_sum && nZ0 + 2 > s.cap) {
       if (threadIdx.x == 0) raise_range(p.st, 32LL * (nZ0 + 2 - s.cap));
       return;
     }
     const int32_t sv = p.rhs.sign[i];
-    for (int d = threadIdx.x; d < nZ0; d += NT_SOLVE) {
+    for (int d = threadIdx.x; d < nZ0; d += NT) {
+      if (small_sum) {
+        s.cs[d] = (long long)vl[d];  // the rhs mantissa itself
+        continue;
+      }
       uint32_t mv = 0;
       if (!vz) {
         const long long li = d - q0;
@@ -287,14 +306,19 @@ __global__ void __launch_bounds__(NT_SOLVE) k_solve_block(SolveParams p, const u
       s.cs[d] = (sv ? -(long long)mv : (long long)mv) - cv;
     }
     __syncthreads();
-    const bool neg = mp::resolve<NT_SOLVE>(s.cs, nZ0, s.Z, *s.red);
+    const bool neg = small_sum ? sv != 0 : mp::resolve<NT>(s.cs, nZ0, s.Z, *s.red);
+    if (small_sum) {
+      for (int l = threadIdx.x; l < L + 2; l += NT) s.Z[l] = l < L ? vl[l] : 0;
+      __syncthreads();
+    }
     const int sgn = neg ? -1 : 1;
-    const mp::Rounded S = mp::round_rne<NT_SOLVE>(s.Z, nZ0 + 2, G, L, s.mant, w);
+    const mp::Rounded S = small_sum ? mp::round_rne<NT>(s.Z, L, p.rhs.exp[i], L, s.mant, w)
+                                    : mp::round_rne<NT>(s.Z, nZ0 + 2, G, L, s.mant, w);
     uint32_t *outl = p.out.limbs + (long long)i * L;
     uint32_t *ya = b.Ys + step * Wv;
     if (!S.nonzero) {
-      for (int l = threadIdx.x; l < L; l += NT_SOLVE) outl[l] = 0;
-      for (int l = threadIdx.x; l < Wv; l += NT_SOLVE) ya[l] = 0;
+      for (int l = threadIdx.x; l < L; l += NT) outl[l] = 0;
+      for (int l = threadIdx.x; l < Wv; l += NT) ya[l] = 0;
       if (threadIdx.x == 0) {
         p.out.sign[i] = 0;
         p.out.exp[i] = 0;
@@ -304,13 +328,13 @@ __global__ void __launch_bounds__(NT_SOLVE) k_solve_block(SolveParams p, const u
       continue;
     }
     const long long iidx = tri_idx(i, i, N);
-    for (int l = threadIdx.x; l < L; l += NT_SOLVE) s.rm[l] = p.R.limbs[iidx * L + l];
-    for (int l = threadIdx.x; l < L + 2; l += NT_SOLVE) s.V[l] = p.recip[(long long)i * (L + 2) + l];
+    for (int l = threadIdx.x; l < L; l += NT) s.rm[l] = p.R.limbs[iidx * L + l];
+    for (int l = threadIdx.x; l < L + 2; l += NT) s.V[l] = p.recip[(long long)i * (L + 2) + l];
     __syncthreads();
     bool ok = true;
     const mp::Rounded Q =
-        mp::div_rne<NT_SOLVE>(s.mant, S.exp, s.rm, p.R.exp[iidx], s.V, L, s.res, w, s.big, s.q, &ok);
-    for (int l = threadIdx.x; l < L; l += NT_SOLVE) outl[l] = s.res[l];
+        mp::div_rne<NT>(s.mant, S.exp, s.rm, p.R.exp[iidx], s.V, L, s.res, w, s.big, s.q, &ok);
+    for (int l = threadIdx.x; l < L; l += NT) outl[l] = s.res[l];
     if (threadIdx.x == 0) {
       p.out.sign[i] = sgn < 0 ? 1 : 0;
       p.out.exp[i] = Q.exp;
@@ -324,7 +348,7 @@ __global__ void __launch_bounds__(NT_SOLVE) k_solve_block(SolveParams p, const u
         if (threadIdx.x == 0) raise_range(p.st, sh < 0 ? -sh : sh + P - 32LL * Wv);
         return;
       }
-      mp::shl<NT_SOLVE>(s.res, L, sh, ya, Wv);
+      mp::shl<NT>(s.res, L, sh, ya, Wv);
     }
     __syncthreads();
   }
@@ -498,25 +522,50 @@ cudaError_t set_smem(const void *fn, size_t bytes) {
 
 }  // namespace
 
-cudaError_t launch_solve_entry(const SolveParams &p, int i, cudaStream_t s) {
+// threads per CTA of the single-CTA solve kernels (templated for tuning; fewer
+// threads measured slower at every precision: the work of an entry is
+// parallel over its result columns)
+int solve_threads(int L) {
+  (void)L;
+  return NT_SOLVE;
+}
+
+template <int NT>
+cudaError_t launch_solve_entry_t(const SolveParams &p, int i, cudaStream_t s) {
   const size_t smem = ssmem_size(p.L, p.C, false);
-  cudaError_t e = set_smem((const void *)k_solve_entry, smem);
+  cudaError_t e = set_smem((const void *)k_solve_entry<NT>, smem);
   if (e != cudaSuccess) return e;
-  k_solve_entry<<<1, NT_SOLVE, smem, s>>>(p, i);
+  k_solve_entry<NT><<<1, NT, smem, s>>>(p, i);
   return cudaGetLastError();
+}
+
+cudaError_t launch_solve_entry(const SolveParams &p, int i, cudaStream_t s) {
+  switch (solve_threads(p.L)) {
+    case 256: return launch_solve_entry_t<256>(p, i, s);
+    default: return launch_solve_entry_t<NT_SOLVE>(p, i, s);
+  }
 }
 
 size_t solve_block_smem(int L, int C, int W, int Wv, int nb) {
   return block_smem_size(L, C, W, Wv, nb, nullptr, nullptr);
 }
 
+template <int NT>
+cudaError_t launch_solve_block_t(const SolveParams &p, const uint32_t *A, const int32_t *Asign, int B0, int B1,
+                                 cudaStream_t s) {
+  const size_t smem = block_smem_size(p.L, p.C, p.W, p.Wv, B1 - B0, nullptr, nullptr);
+  cudaError_t e = set_smem((const void *)k_solve_block<NT>, smem);
+  if (e != cudaSuccess) return e;
+  k_solve_block<NT><<<1, NT, smem, s>>>(p, A, Asign, B0, B1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_solve_block(const SolveParams &p, const uint32_t *A, const int32_t *Asign, int B0, int B1,
                                cudaStream_t s) {
-  const size_t smem = block_smem_size(p.L, p.C, p.W, p.Wv, B1 - B0, nullptr, nullptr);
-  cudaError_t e = set_smem((const void *)k_solve_block, smem);
-  if (e != cudaSuccess) return e;
-  k_solve_block<<<1, NT_SOLVE, smem, s>>>(p, A, Asign, B0, B1);
-  return cudaGetLastError();
+  switch (solve_threads(p.L)) {
+    case 256: return launch_solve_block_t<256>(p, A, Asign, B0, B1, s);
+    default: return launch_solve_block_t<NT_SOLVE>(p, A, Asign, B0, B1, s);
+  }
 }
 
 cudaError_t launch_vec_exprange(int n, MpArr v, int L, const long long *off, int scaled, long long *out2,

@@ -33,6 +33,7 @@
 #include "hk_mp.cuh"
 #include <algorithm>
 #include <climits>
+#include <cstdio>
 #include <cstdlib>
 #include <mutex>
 #include <set>
@@ -586,7 +587,13 @@ cudaError_t launch_uc(const UpdParams &p, cudaStream_t s) {
   const int nz = (p.t1 - p.t0 + p.tchunk - 1) / p.tchunk;
   dim3 grid((p.nunits + UNT - 1) / UNT, p.nout, nz);
   k_update<UCT><<<grid, UNT + 32, smem, s>>>(p);
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+#ifdef HK_CHECKED
+  if (e != cudaSuccess)
+    fprintf(stderr, "[hk checked] k_update<%d> mode %d grid (%u,%u,%u) smem %zu cx %d cy %d uc %d upc %d nsub %d nxb %d: %s\n",
+            UCT, p.mode, grid.x, grid.y, grid.z, smem, p.cx, p.cy, p.uc, p.upc, p.nsub, p.nxb, cudaGetErrorString(e));
+#endif
+  return e;
 }
 
 }  // namespace
