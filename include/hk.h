@@ -177,7 +177,9 @@ int hk_get_timings(hk_ctx *ctx, double *out, int n);
  * products the update executes per P-bit multiply-accumulate, out[5] 1 if the
  * last hk_smallest_eig with iters = 0 met the convergence test, out[6] and
  * out[7] the largest and mean window width in limbs of the solution vectors
- * in that hk_smallest_eig (the exact products of a solve cost W x that width). */
+ * in that hk_smallest_eig (the exact products of a solve cost W x that width),
+ * out[8] how many window widenings of the last hk_factor resumed at the
+ * failing block (re-aligning the finished rows) instead of restarting. */
 int hk_get_stats(hk_ctx *ctx, int64_t *out, int n);
 
 /* ----- measurement hook ------------------------------------------------------
@@ -261,6 +263,20 @@ int hk_mlp_adam(float *params, const float *grad, float *m, float *v, int n, int
 int hk_mlp_train(float *params, float *m, float *v, float *grad, const float *x, const float *t,
                  const float *w, int B, int steps, int step0, float lr, float beta1, float beta2,
                  float eps, float *loss_hist, void *work, size_t work_bytes, void *stream);
+
+/* Load a trained predictor network into the context: params = HK_MLP_NPARAMS
+ * host floats (layout above), scales = 10 host doubles: feature means and
+ * standard deviations (2 + 2; features log2 N - 8 and log2 beta) and target
+ * means and standard deviations (3 + 3; targets (bits - 128)/N,
+ * log2(lambda_min)/N and log2(iterations)).  Copied; the context keeps them. */
+int hk_set_predictor(hk_ctx *ctx, const float *params, const double *scales);
+
+/* Predict for `count` instances (host arrays N[count], beta[count] > 0): out3
+ * (host, count x 3 floats) receives the required precision in bits (before any
+ * safety margin), log2 lambda_min and the iteration count to convergence.
+ * Runs the network on the context's device and stream; returns after the
+ * results are on the host.  HK_ERR_STATE if no network was loaded. */
+int hk_predict(hk_ctx *ctx, int count, const double *N, const double *beta, float *out3);
 
 #ifdef __cplusplus
 }

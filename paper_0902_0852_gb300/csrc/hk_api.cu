@@ -6,6 +6,7 @@
 #include "hk_internal.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <climits>
 #include <cstdlib>
@@ -72,6 +73,8 @@ struct hk_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   Arena base_arena, fac_arena, sol_arena;
+  Arena res_arena;          // R, its signs and the reciprocals: kept across window widenings
+  int res_N = 0, res_L = 0;
   char *ws = nullptr;
   size_t ws_bytes = 0;
   // problem
@@ -92,7 +95,12 @@ struct hk_ctx {
   bool use_graph = false;    // capture each factorisation in a CUDA graph
   cudaStream_t cap_stream = nullptr;  // capture stream when `stream` is a default stream
   int max_iters = 200;       // step cap of hk_smallest_eig(iters = 0)
+  float *pred_params = nullptr;  // predictor network on the device (hk_set_predictor)
+  double pred_scales[10] = {0};
+  float *pred_buf = nullptr;     // inputs and outputs of hk_predict
+  int pred_cap = 0;
   long long fuse_ww = 160000;  // solve blocks run in one launch when W * Wv is at most this
+  long long solve_margin = 256;  // first-attempt margin of a solve block's vector window (bits)
   long long wv_max = 0, wv_sum = 0, wv_count = 0;  // solve window widths of the last eig
   int eig_converged = 0;     // last hk_smallest_eig(iters = 0) met the convergence test
   bool autotune = false;     // time candidate update schedules per shape
@@ -122,6 +130,7 @@ struct hk_ctx {
   double t_factor = 0, t_eig = 0;
   long long launches = 0;
   int widenings = 0;
+  int resumes = 0;  // widenings that resumed at a later block instead of restarting
   long long top_margin = 0;  // extra bits above the a priori column bounds
   bool timing = true;
 };
@@ -467,6 +476,7 @@ cudaError_t reset_status(hk_ctx *c) {
   DevStatus s;
   std::memset(&s, 0, sizeof(s));
   s.bad_row = INT_MAX;
+  s.range_row = INT_MAX;
   return cudaMemcpyAsync(c->st, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream);
 }
 
@@ -476,9 +486,11 @@ __global__ void k_col_grid(int N, const long long *colU, int W, long long *colG)
 }
 
 // one attempt of the blocked factorisation with window width c->W
-int factor_enqueue(hk_ctx *c, const Sched &sc);
+int factor_enqueue(hk_ctx *c, const Sched &sc, int r_start);
 
-int factor_attempt(hk_ctx *c) {
+// one attempt of the factorisation from block row r_start (> 0: resume after a
+// window widening; rows above it are final and only re-aligned)
+int factor_attempt(hk_ctx *c, int r_start) {
   const int N = c->N, L = c->L, W = c->W, nb = c->nb;
   const size_t NT = (size_t)N * (N + 1) / 2;
   const int levels = c->update_path == 1 ? 0 : c->kar_levels;
@@ -487,15 +499,23 @@ int factor_attempt(hk_ctx *c) {
   CK(sched_for(c, W, W, levels, &sc));
   c->C = sc.C;
   const long long maxout = rows_outputs(N, 0, std::min(nb, N));
+  if (c->res_N != N || c->res_L != L) {
+    // R (floating form), signs and reciprocals depend on (N, P) only: they
+    // survive a widening of the window, which then resumes instead of restarting
+    c->res_arena.release();
+    c->res_N = c->res_L = 0;
+    CK(alloc_mp(c, c->res_arena, &c->R, NT, L));
+    CK(alloc(c, c->res_arena, &c->Asign, NT));
+    CK(alloc(c, c->res_arena, &c->recip, (size_t)N * (L + 2)));
+    c->res_N = N;
+    c->res_L = L;
+  }
   if (c->fac_N != N || c->fac_L != L || c->fac_W != W || c->fac_levels != levels) {
     // (re)allocate only when the shape changed; in caller-workspace mode the
     // bump arena keeps the old region (a widening costs one more copy)
     c->fac_arena.release();
     c->fac_N = c->fac_L = c->fac_W = 0;
-    CK(alloc_mp(c, c->fac_arena, &c->R, NT, L));
     CK(alloc(c, c->fac_arena, &c->A, NT * (size_t)W));
-    CK(alloc(c, c->fac_arena, &c->Asign, NT));
-    CK(alloc(c, c->fac_arena, &c->recip, (size_t)N * (L + 2)));
     CK(alloc(c, c->fac_arena, &c->colsum, (size_t)maxout * c->C));
     c->Aexp = nullptr;
     if (levels > 0) CK(alloc(c, c->fac_arena, &c->Aexp, NT * (size_t)c->kl.stride));
@@ -508,7 +528,7 @@ int factor_attempt(hk_ctx *c) {
     c->fac_levels = levels;
   }
   CK(reset_status(c));
-  if (!c->use_graph) return factor_enqueue(c, sc);
+  if (!c->use_graph) return factor_enqueue(c, sc, r_start);
   // capture the whole launch sequence of this factorisation in a CUDA graph
   // and replay it (no host synchronisation happens inside the sequence)
   const bool timing = c->timing;
@@ -529,7 +549,7 @@ int factor_attempt(hk_ctx *c) {
     c->timing = timing;
     return HK_ERR_CUDA;
   }
-  const int rc = factor_enqueue(c, sc);
+  const int rc = factor_enqueue(c, sc, r_start);
   const cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
   c->stream = run;
   c->timing = timing;
@@ -548,7 +568,7 @@ int factor_attempt(hk_ctx *c) {
 }
 
 // the factorisation's launch sequence (asynchronous on the context stream)
-int factor_enqueue(hk_ctx *c, const Sched &sc) {
+int factor_enqueue(hk_ctx *c, const Sched &sc, int r_start) {
   const int N = c->N, L = c->L, W = c->W, nb = c->nb;
   const int levels = c->update_path == 1 ? 0 : c->kar_levels;
   CK(launch_col_tops(N, L, c->top_margin, c->mom, c->colU, c->st, c->stream));
@@ -592,7 +612,12 @@ int factor_enqueue(hk_ctx *c, const Sched &sc) {
   const long long cta_per_out = (sc.n + UNT - 1) / UNT;
   const long long target = 6LL * sm_count(c) * 3;
 
-  for (int r0 = 0; r0 < N; r0 += nb) {
+  if (r_start > 0) {
+    CK(launch_realign(pp, r_start, c->stream));
+    DBG(c, "realign", r_start, W);
+    c->launches++;
+  }
+  for (int r0 = r_start; r0 < N; r0 += nb) {
     const int r1 = std::min(N, r0 + nb);
     const long long nout = rows_outputs(N, r0, r1);
     CK(cudaMemsetAsync(c->colsum, 0, sizeof(long long) * nout * c->C, c->stream));
@@ -712,7 +737,7 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
   sp.out = out;
   sp.back = back ? 1 : 0;
   sp.st = c->st;
-  long long margin = 256;
+  long long margin = c->solve_margin;  // bits above and below the known entries' range
   for (size_t bi = 0; bi < blocks.size(); bi++) {
     const int B0 = blocks[bi].first, B1 = blocks[bi].second;
     const int k0 = back ? B1 : 0, k1 = back ? N : B0;  // known entries
@@ -1018,7 +1043,10 @@ void hk_destroy(hk_ctx *c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->sol_arena.release();
   c->fac_arena.release();
+  c->res_arena.release();
   c->base_arena.release();
+  if (c->pred_params) cudaFree(c->pred_params);
+  if (c->pred_buf) cudaFree(c->pred_buf);
   for (auto &p : c->evpool) {
     if (p.a) cudaEventDestroy(p.a);
     if (p.b) cudaEventDestroy(p.b);
@@ -1055,7 +1083,10 @@ int hk_set_workspace(hk_ctx *c, void *dev_ptr, size_t bytes) {
   cudaSetDevice(c->device);
   c->sol_arena.release();
   c->fac_arena.release();
+  c->res_arena.release();
   c->base_arena.release();
+  c->res_N = c->res_L = 0;
+  c->fac_N = c->fac_L = c->fac_W = 0;
   c->ws = reinterpret_cast<char *>(dev_ptr);
   c->ws_bytes = bytes;
   c->base_arena.base = c->ws;
@@ -1097,6 +1128,8 @@ int hk_load_moments_flat(hk_ctx *c, int N, int bnum, int bden, int P, const int3
   if (!same) {
     c->sol_arena.release();
     c->fac_arena.release();
+    c->res_arena.release();
+    c->res_N = c->res_L = 0;
     c->base_arena.release();
     if (c->ws) {
       c->base_arena.base = c->ws;
@@ -1151,8 +1184,13 @@ int hk_factor(hk_ctx *c, int *bad_row) {
   c->factored = false;
   c->launches = 0;
   c->widenings = 0;
+  c->resumes = 0;
   c->t_phase[0] = c->t_phase[1] = c->t_phase[2] = 0;
-  c->W = round4(c->L + (c->N + 128 + 31) / 32);
+  // window: P bits plus the spread of a column (at most about N bits for
+  // beta = 1) plus 128; HK_WINDOW_SLACK overrides the extra bits (tests)
+  long long slack = c->N + 128;
+  if (const char *e = getenv("HK_WINDOW_SLACK")) slack = std::max(0LL, atoll(e));
+  c->W = round4(c->L + (slack + 31) / 32);
   c->top_margin = 0;
   if (const char *e = getenv("HK_NB")) c->nb = std::max(1, atoi(e));  // panel block rows (tuning)
   if (const char *e = getenv("HK_KARATSUBA")) c->kar_levels = std::min(2, std::max(0, atoi(e)));  // (tuning)
@@ -1160,10 +1198,12 @@ int hk_factor(hk_ctx *c, int *bad_row) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   int result = HK_ERR_RANGE;
-  for (int attempt = 0; attempt < 4; attempt++) {
+  int r_start = 0;
+  c->t_factor = 0;
+  for (int attempt = 0; attempt < 6; attempt++) {
     c->evused = 0;
     cudaEventRecord(e0, c->stream);
-    int rc = factor_attempt(c);
+    int rc = factor_attempt(c, r_start);
     cudaEventRecord(e1, c->stream);
     if (rc != HK_OK) {
       result = rc;
@@ -1173,24 +1213,28 @@ int hk_factor(hk_ctx *c, int *bad_row) {
     cudaEventSynchronize(e1);
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
-    c->t_factor = ms;
-    c->t_phase[0] = c->t_phase[1] = 0;
+    c->t_factor += ms;  // every attempt counts
     ev_collect(c);
     if (st.timeout) {
       result = HK_ERR_TIMEOUT;
       break;
     }
-    // a window failure invalidates everything after it (including a later
-    // pivot test): widen the window below and above, and start again
+    // a window failure stops the sequence at its launch: widen the window
+    // below and above, re-align the finished rows above the failing block and
+    // resume there (rows above it are final in floating form)
     if (st.range_fail) {
       // the sequence stops at the first failing launch, so the shortfall seen
       // is a lower bound for the rows after it: widen generously (twice the
-      // shortfall, at least N/2 bits) so that one restart usually suffices
+      // shortfall, at least N/2 bits) so that one resumption usually suffices
       const long long want = std::max(2 * st.need_bits, (long long)c->N / 2) + 64;
       const long long delta = (want + 31) / 32 * 32;
       c->top_margin += delta;
       c->W = round4(c->W + 2 * delta / 32);
       c->widenings++;
+      const int row = st.range_row;
+      r_start = (row != INT_MAX && row >= 0 && row < c->N) ? (row / c->nb) * c->nb : 0;
+      if (r_start > 0 && c->use_graph) r_start = 0;  // graphs record whole factorisations
+      if (r_start > 0) c->resumes++;
       continue;
     }
     if (st.code == ST_NOT_PD) {
@@ -1295,6 +1339,7 @@ int hk_smallest_eig(hk_ctx *c, int iters, hk_mp *lambda_min, int *iters_used) {
   cudaSetDevice(c->device);
   const int T = iters > 0 ? iters : c->max_iters;
   if (const char *e = getenv("HK_FUSE_WW")) c->fuse_ww = atoll(e);  // (tuning and tests)
+  if (const char *e = getenv("HK_SOLVE_MARGIN")) c->solve_margin = std::max(32LL, atoll(e));  // (tuning)
   c->eig_converged = 0;
   c->wv_max = c->wv_sum = c->wv_count = 0;
   int rc = ensure_solve_buffers(c, T);
@@ -1402,16 +1447,17 @@ int hk_get_stats(hk_ctx *c, int64_t *out, int n) {
   const int ns = kar_subprobs(kl, sub);
   int64_t per_mac = 0;
   for (int k = 0; k < ns; k++) per_mac += (int64_t)sub[k].wx * sub[k].wy;
-  const int64_t v[8] = {c->launches,
+  const int64_t v[9] = {c->launches,
                         c->W,
                         c->widenings,
                         c->update_path == 1 ? 0 : c->kar_levels,
                         per_mac,
                         c->eig_converged,
                         c->wv_max,
-                        c->wv_count ? c->wv_sum / c->wv_count : 0};
-  for (int k = 0; k < n && k < 8; k++) out[k] = v[k];
-  for (int k = 8; k < n; k++) out[k] = 0;
+                        c->wv_count ? c->wv_sum / c->wv_count : 0,
+                        c->resumes};
+  for (int k = 0; k < n && k < 9; k++) out[k] = v[k];
+  for (int k = 9; k < n; k++) out[k] = 0;
   return HK_OK;
 }
 
@@ -1420,6 +1466,52 @@ int hk_selftest_mp(int op, int L, const uint32_t *x, int nx, int64_t ex, const u
   if (!x || !out || !eo || (ny > 0 && !y)) return HK_ERR_ARG;
   const int rc = hk::selftest_mp(op, L, x, nx, ex, y, ny, ey, out, eo);
   return rc == 0 ? HK_OK : (rc == 1 ? HK_ERR_ARG : HK_ERR_CUDA);
+}
+
+int hk_set_predictor(hk_ctx *c, const float *params, const double *scales) {
+  if (!c || !params || !scales) return HK_ERR_ARG;
+  for (int k = 0; k < 10; k++)
+    if (!std::isfinite(scales[k]) || ((k == 2 || k == 3 || k >= 7) && scales[k] <= 0)) return HK_ERR_ARG;
+  cudaSetDevice(c->device);
+  if (!c->pred_params) CK(cudaMalloc(&c->pred_params, sizeof(float) * HK_MLP_NPARAMS));
+  CK(cudaMemcpyAsync(c->pred_params, params, sizeof(float) * HK_MLP_NPARAMS, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 10; k++) c->pred_scales[k] = scales[k];
+  return HK_OK;
+}
+
+int hk_predict(hk_ctx *c, int count, const double *N, const double *beta, float *out3) {
+  if (!c || count < 0 || (count > 0 && (!N || !beta || !out3))) return HK_ERR_ARG;
+  if (!c->pred_params) return HK_ERR_STATE;
+  if (count == 0) return HK_OK;
+  cudaSetDevice(c->device);
+  const double *sc = c->pred_scales;  // x mean[2], x std[2], y mean[3], y std[3]
+  std::vector<float> x((size_t)count * 2), y((size_t)count * 3);
+  for (int k = 0; k < count; k++) {
+    if (!(N[k] >= 1) || !(beta[k] > 0)) return HK_ERR_ARG;
+    x[2 * k] = (float)((std::log2(N[k]) - 8.0 - sc[0]) / sc[2]);
+    x[2 * k + 1] = (float)((std::log2(beta[k]) - sc[1]) / sc[3]);
+  }
+  if (count > c->pred_cap) {
+    if (c->pred_buf) cudaFree(c->pred_buf);
+    c->pred_buf = nullptr;
+    c->pred_cap = 0;
+    CK(cudaMalloc(&c->pred_buf, sizeof(float) * 5 * (size_t)count));
+    c->pred_cap = count;
+  }
+  float *dx = c->pred_buf, *dy = c->pred_buf + 2 * (size_t)count;
+  CK(cudaMemcpyAsync(dx, x.data(), sizeof(float) * x.size(), cudaMemcpyHostToDevice, c->stream));
+  const int rc = hk_mlp_forward(c->pred_params, dx, count, dy, c->stream);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(y.data(), dy, sizeof(float) * y.size(), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < count; k++) {
+    const double t0 = y[3 * k] * sc[7] + sc[4], t1 = y[3 * k + 1] * sc[8] + sc[5], t2 = y[3 * k + 2] * sc[9] + sc[6];
+    out3[3 * k] = (float)(t0 * N[k] + 128.0);  // (bits - 128) / N
+    out3[3 * k + 1] = (float)(t1 * N[k]);      // log2(lambda_min) / N
+    out3[3 * k + 2] = (float)std::exp2(t2);    // log2(iterations)
+  }
+  return HK_OK;
 }
 
 }  // extern "C"

@@ -15,7 +15,7 @@ struct DevStatus {
   int timeout;       // a bounded wait ran out (count)
   long long need_bits;  // largest shortfall seen in bits (atomicMax)
   int check_site;    // checked builds: first failed bounds check (site id), else 0
-  int check_pad;
+  int range_row;     // first factor row whose entry did not fit the window (atomicMin)
   long long check_a, check_b;  // the failed check's index and limit
 };
 

@@ -127,6 +127,9 @@ cudaError_t launch_col_tops(int N, int L, long long top_margin, MpArr mom, long 
                             cudaStream_t s);
 cudaError_t launch_diag(const PanelParams &p, int i, cudaStream_t s);
 cudaError_t launch_offdiag(const PanelParams &p, int i, cudaStream_t s);
+// Re-align (and expand) the finished entries of rows t < r0 on the current
+// column grids, from the floating-point R.
+cudaError_t launch_realign(const PanelParams &p, int r0, cudaStream_t s);
 size_t panel_smem_diag(int L, int C);
 size_t panel_smem_row(int L, int C);
 

@@ -161,7 +161,10 @@ __global__ void __launch_bounds__(NT) k_diag(PanelParams p, int i) {
   int nZ = 0;
   const int sgn = form_exact<NT>(s, colrow, p.C, p.mom.sign[mk], p.mom.exp[mk],
                                       p.mom.limbs + (long long)mk * L, L, 2 * gi, p.st, &nZ);
-  if (sgn == 0) return;
+  if (sgn == 0) {
+    if (threadIdx.x == 0) atomicMin(&p.st->range_row, i);
+    return;
+  }
   const mp::Rounded S = mp::round_rne<NT>(s.Z, nZ, 2 * gi, L, s.mant, w);
   if (!S.nonzero || sgn < 0) {
     if (threadIdx.x == 0) {
@@ -183,7 +186,8 @@ __global__ void __launch_bounds__(NT) k_diag(PanelParams p, int i) {
     p.Asign[idx] = 0;
     if (!ok) atomicAdd(&p.st->timeout, 1);
   }
-  align_entry<NT>(s.rm, L, Rr.exp, false, gi, p.W, p.A + idx * p.W, p.st);
+  if (!align_entry<NT>(s.rm, L, Rr.exp, false, gi, p.W, p.A + idx * p.W, p.st) && threadIdx.x == 0)
+    atomicMin(&p.st->range_row, i);
   __syncthreads();
   if (p.kl.levels > 0)
     expand_entry<NT>(p.A + idx * p.W, p.kl, p.Aexp + idx * p.kl.stride, s.cs, s.Z, s.big, *s.red);
@@ -220,7 +224,10 @@ __global__ void __launch_bounds__(NT) k_offdiag(PanelParams p, int i) {
   int nZ = 0;
   const int sgn = form_exact<NT>(s, colrow, p.C, p.mom.sign[mk], p.mom.exp[mk],
                                      p.mom.limbs + (long long)mk * L, L, gi + gj, p.st, &nZ);
-  if (sgn == 0) return;
+  if (sgn == 0) {
+    if (threadIdx.x == 0) atomicMin(&p.st->range_row, i);
+    return;
+  }
   const mp::Rounded S = mp::round_rne<NT>(s.Z, nZ, gi + gj, L, s.mant, w);
   const long long idx = tri_idx(i, j, N);
   const long long iidx = tri_idx(i, i, N);
@@ -248,9 +255,51 @@ __global__ void __launch_bounds__(NT) k_offdiag(PanelParams p, int i) {
     p.Asign[idx] = sgn < 0 ? 1 : 0;
     if (!ok) atomicAdd(&p.st->timeout, 1);
   }
-  if (align_entry<NT>(s.res, L, Q.exp, false, gj, p.W, p.A + idx * p.W, p.st) && p.kl.levels > 0) {
+  const bool fits = align_entry<NT>(s.res, L, Q.exp, false, gj, p.W, p.A + idx * p.W, p.st);
+  if (!fits && threadIdx.x == 0) atomicMin(&p.st->range_row, i);
+  if (fits && p.kl.levels > 0) {
     __syncthreads();
     expand_entry<NT>(p.A + idx * p.W, p.kl, p.Aexp + idx * p.kl.stride, s.cs, s.Z, s.big, *s.red);
+  }
+}
+
+// Re-writes the finished entries of rows t < r0 (packed indices [0, E)) on the
+// column grids of a widened window: aligned from the floating-point R, then
+// expanded.  Lets a window failure resume at its block instead of restarting.
+constexpr int NT_RA = 128;
+__global__ void __launch_bounds__(NT_RA) k_realign(PanelParams p, long long E) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int t_s;
+  const long long e = blockIdx.x;
+  if (e >= E) return;
+  const int N = p.N, L = p.L;
+  if (threadIdx.x == 0) {  // row of packed index e: largest t with tri_idx(t, t) <= e
+    int lo = 0, hi = N - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (tri_idx(mid, mid, N) <= e) lo = mid; else hi = mid - 1;
+    }
+    t_s = lo;
+  }
+  __syncthreads();
+  const int t = t_s;
+  const int j = (int)(e - tri_idx(t, t, N)) + t;
+  const uint32_t *mant = p.R.limbs + e * L;
+  bool zero = true;
+  for (int l = 0; l < L; l++) zero &= (mant[l] == 0);
+  const long long gj = p.colU[j] - 32LL * p.W;
+  if (!align_entry<NT_RA>(mant, L, p.R.exp[e], zero, gj, p.W, p.A + e * p.W, p.st)) {
+    if (threadIdx.x == 0) atomicMin(&p.st->range_row, t);
+    return;
+  }
+  if (threadIdx.x == 0) p.Asign[e] = p.R.sign[e];
+  if (p.kl.levels > 0) {
+    __syncthreads();
+    const int h1 = p.W / 2 + 8;
+    mp::Red *red = reinterpret_cast<mp::Red *>(smem_raw);
+    long long *cs = reinterpret_cast<long long *>(smem_raw + ((sizeof(mp::Red) + 15) / 16) * 16);
+    uint32_t *t1 = reinterpret_cast<uint32_t *>(cs + h1);
+    expand_entry<NT_RA>(p.A + e * p.W, p.kl, p.Aexp + e * p.kl.stride, cs, t1, t1 + h1, *red);
   }
 }
 
@@ -304,6 +353,17 @@ static cudaError_t launch_offdiag_t(const PanelParams &p, int i, cudaStream_t s)
 cudaError_t launch_offdiag(const PanelParams &p, int i, cudaStream_t s) {
   if (i + 1 >= p.N) return cudaSuccess;
   return launch_offdiag_t<NT_ROW>(p, i, s);
+}
+
+cudaError_t launch_realign(const PanelParams &p, int r0, cudaStream_t s) {
+  const long long E = tri_idx(r0, r0, p.N);
+  if (r0 <= 0 || E <= 0) return cudaSuccess;
+  const int h1 = p.W / 2 + 8;
+  const size_t smem = ((sizeof(mp::Red) + 15) / 16) * 16 + (size_t)h1 * 8 + (size_t)h1 * 4 * 2;
+  cudaError_t e = set_smem((const void *)k_realign, smem);
+  if (e != cudaSuccess) return e;
+  k_realign<<<(unsigned)E, NT_RA, smem, s>>>(p, E);
+  return cudaGetLastError();
 }
 
 }  // namespace hk

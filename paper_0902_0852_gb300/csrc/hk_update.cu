@@ -549,9 +549,14 @@ void choose_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc_out, int
   int uc_force = 0, upc_force = 0;
   if (const char *e = getenv("HK_UC")) uc_force = atoi(e);
   if (const char *e = getenv("HK_UPC")) upc_force = atoi(e);
-  // inner-loop limb products per clock per SM by stripe width (measured on GB300)
+  // relative limb-product slot rates by stripe width and the per-unit cost
+  // (window load, stage bookkeeping) in slots per stripe column, fitted to
+  // factorisation timings on GB300 (N = 1000, W = 804, two Karatsuba levels,
+  // seven (stripe, chunk) schedules); chunks of one stripe width measured
+  // slower than the model says, so chunks start at two
   const int ucs[3] = {7, 9, 11};
-  const double speed[3] = {21.5, 22.7, 23.4};
+  const double speed[3] = {41.7, 45.9, 45.1};
+  const double unit_cost = 1.75;
   int best_uc = UC, best_upc = 4 * UC;
   double best = 1e300;
   for (int ui = 0; ui < 3; ui++) {
@@ -561,7 +566,7 @@ void choose_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc_out, int
       if (upc_force && upc != upc_force) continue;
       const int n = build_units(sub, nsub, uc, upc, nullptr, 0);
       const int blocks = (n + UNT - 1) / UNT;
-      const double cost = ((double)blocks * UNT * upc * uc + (double)n * 12 * uc) / speed[ui];
+      const double cost = ((double)blocks * UNT * upc * uc + (double)n * unit_cost * uc) / speed[ui];
       if (cost < best) {
         best = cost;
         best_uc = uc;

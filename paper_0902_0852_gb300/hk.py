@@ -29,6 +29,7 @@ EXPORTS = [
     "hk_probe_int_peaks", "hk_mp_op_noalloc", "hk_set_update_path",
     "hk_set_option", "hk_batch_solve",
     "hk_mlp_workspace_bytes", "hk_mlp_forward", "hk_mlp_loss_grad", "hk_mlp_adam", "hk_mlp_train",
+    "hk_set_predictor", "hk_predict",
 ]
 
 
@@ -81,6 +82,8 @@ def lib():
         L.hk_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, sz, vp]
         L.hk_mlp_adam.argtypes = [vp, vp, vp, vp, i32, i32, f32, f32, f32, f32, vp]
         L.hk_mlp_train.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, f32, f32, f32, f32, vp, vp, sz, vp]
+        L.hk_set_predictor.argtypes = [vp, vp, vp]
+        L.hk_predict.argtypes = [vp, i32, vp, vp, vp]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype if name in ("hk_destroy", "hk_strerror") else i32
         L.hk_mlp_workspace_bytes.restype = sz
@@ -238,10 +241,11 @@ def hk_get_timings(ctx):
 
 
 def hk_get_stats(ctx):
-    out = (ctypes.c_int64 * 8)()
-    _check(lib().hk_get_stats(ctx, out, 8), "hk_get_stats")
+    out = (ctypes.c_int64 * 9)()
+    _check(lib().hk_get_stats(ctx, out, 9), "hk_get_stats")
     return {"launches": out[0], "W": out[1], "widenings": out[2], "karatsuba_levels": out[3],
-            "limbprod_per_mac": out[4], "converged": out[5], "solve_wv_max": out[6], "solve_wv_mean": out[7]}
+            "limbprod_per_mac": out[4], "converged": out[5], "solve_wv_max": out[6], "solve_wv_mean": out[7],
+            "resumes": out[8]}
 
 
 def hk_selftest_mp(op, L, x, ex=0, y=None, ey=0):
@@ -429,3 +433,22 @@ def hk_mlp_train(params, m, v, grad, x, t, w, steps, step0, lr, work, loss_hist=
     _check(lib().hk_mlp_train(_dp(params), _dp(m), _dp(v), _dp(grad), _dp(x), _dp(t), _dp(w), x.shape[0], steps,
                               step0, lr, beta1, beta2, eps, _dp(loss_hist), _dp(work),
                               work.numel() * work.element_size(), _stream(stream)), "hk_mlp_train")
+
+
+def hk_set_predictor(ctx, params, x_mean, x_std, y_mean, y_std):
+    """Load a trained network (host float32[HK_MLP_NPARAMS]) and its scalings."""
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    sc = np.ascontiguousarray(np.concatenate([x_mean, x_std, y_mean, y_std]).astype(np.float64))
+    _check(lib().hk_set_predictor(ctx, p.ctypes.data_as(ctypes.c_void_p), sc.ctypes.data_as(ctypes.c_void_p)),
+           "hk_set_predictor")
+
+
+def hk_predict(ctx, Ns, betas):
+    """(bits, log2 lambda_min, iterations) per (N, beta) from the loaded network."""
+    n = len(Ns)
+    N = np.ascontiguousarray(np.asarray(Ns, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
+    out = np.zeros((n, 3), dtype=np.float32)
+    _check(lib().hk_predict(ctx, n, N.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p),
+                            out.ctypes.data_as(ctypes.c_void_p)), "hk_predict")
+    return out

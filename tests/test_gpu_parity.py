@@ -201,3 +201,37 @@ def test_solve_paths_bit_identical(hk, monkeypatch, fuse):
     assert R == Ro
     _, hist_o, _ = oracle.inverse_iteration(Ro, P, T)
     assert hist == hist_o
+
+
+# Slack 0 fails in the first block (a restart).  L = P/32 = 15 leaves exactly
+# one limb (32 bits) of slack after W is rounded up to a multiple of 4; for
+# beta = 3 and 4 the first row's entries spread less than that (at most 18 and
+# 16 bits here) while the diagonal entries of later columns spread up to 68 and
+# 84 bits, so the failure comes in a later block and the factorisation resumes.
+@pytest.mark.parametrize("N,beta,P,slack", [(40, (7, 4), 384, "0"), (57, (3, 1), 512, "0"), (48, (3, 1), 480, "16"),
+                                            (56, (4, 1), 480, "16")])
+def test_window_widening_resumes_bit_identical(hk, monkeypatch, N, beta, P, slack):
+    """A window too narrow for the column spread (forced by HK_WINDOW_SLACK)
+    fails part-way; the factorisation widens it, re-aligns the finished rows
+    and resumes at the failing block (or restarts when that is block 0).  R
+    and the inverse-iteration history still equal the oracle's bit for bit."""
+    monkeypatch.setenv("HK_WINDOW_SLACK", slack)
+    monkeypatch.setenv("HK_NB", "8")
+    m, R, lam, hist, stats = gpu_run(hk, N, beta, P, 5)
+    assert stats["widenings"] >= 1
+    Ro = oracle.cholesky(m, N, P)
+    assert R == Ro
+    _, hist_o, _ = oracle.inverse_iteration(Ro, P, 5)
+    assert hist == hist_o
+    RESUMES.append(stats["resumes"])
+
+
+RESUMES = []
+
+
+def test_some_widening_resumed():
+    """Of the forced widenings above, at least one resumed at a later block
+    (the path that re-aligns finished rows), not only full restarts."""
+    if not RESUMES:
+        pytest.skip("widening cases did not run")
+    assert max(RESUMES) >= 1, RESUMES

@@ -61,3 +61,22 @@ def test_escalation_from_underprovisioned_prediction(pr):
     c = pr.solve_conservative(N, beta)
     assert v["verified"] and len(v["tried"]) > 2
     assert pr.rel_err_bits(v["lam"], c["lam"]) >= pr.AGREE_BITS
+
+
+def test_c_abi_predict_matches_wrapper(pr):
+    """hk_predict (the network behind the C ABI, with its feature and target
+    scalings) gives the same predictions as the Python wrapper."""
+    from paper_0902_0852_gb300 import hk
+    model = pr.load_default()
+    rows = [(40, (7, 4)), (333, (1, 1)), (600, (3, 5)), (1000, (1, 1)), (777, (4, 1))]
+    want = model.predict_raw(rows)
+    ctx = hk.hk_create(0)
+    try:
+        hk.hk_set_predictor(ctx, model.params.cpu().numpy(), model.x_mean, model.x_std, model.y_mean, model.y_std)
+        got = hk.hk_predict(ctx, [N for N, _ in rows], [b[0] / b[1] for _, b in rows])
+    finally:
+        hk.hk_destroy(ctx)
+    for (b, l2, it), g in zip(want, got):
+        assert abs(g[0] - b) <= 1e-3 * abs(b) + 0.5
+        assert abs(g[1] - l2) <= 1e-3 * abs(l2) + 0.05
+        assert abs(g[2] - it) <= 1e-3 * it
