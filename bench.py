@@ -33,7 +33,7 @@ SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.act
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 # DRAM bytes (read + write) per executed limb product of the update kernel, from
 # one ncu capture of the current kernel version; None when not measured.
-UPDATE_TRAFFIC_BYTES_PER_LIMBPROD = 10.0295e9 / (3976 * 256 * 351258)  # k_update_karatsuba_N512_P24576_full.md
+UPDATE_TRAFFIC_BYTES_PER_LIMBPROD = (18.6326e9 + 0.0326e9) / (3976 * 256 * 265833)  # k_update_karatsuba3_N512_P24576_full.md
 
 
 def parse():

@@ -108,7 +108,7 @@ int hk_factor(hk_ctx *ctx, int *bad_row);
 
 /* Select the kernel of the factorisation's trailing update for later
  * hk_factor calls: path 0 (default) = exact product scanning on the integer
- * multiply-add pipe with two Karatsuba levels; path 1 = the same exact
+ * multiply-add pipe with Karatsuba pieces; path 1 = the same exact
  * contraction on the INT8 tensor path (mma.sync m16n8k32 u8 x u8 -> s32 over
  * the bytes of the aligned entries, 64-bit drains).  Both give bit-identical R
  * (the contraction is exact integer arithmetic either way).  Invalidates a
@@ -117,7 +117,9 @@ int hk_set_update_path(hk_ctx *ctx, int path);
 
 /* Options of a context (take effect at the next hk_factor):
  *   HK_OPT_UPDATE_PATH      0 IMAD product scanning (default), 1 INT8 mma.sync
- *   HK_OPT_KARATSUBA        Karatsuba levels of the IMAD update, 0..2 (default 2)
+ *   HK_OPT_KARATSUBA        Karatsuba levels of the IMAD update, 0..3, or -1
+ *                           (default): the depth of least modelled update
+ *                           cost for the window width
  *   HK_OPT_GRAPH            1: capture each factorisation's launch sequence in a
  *                           CUDA graph and replay it (default 0)
  *   HK_OPT_AUTOTUNE         1: choose the update kernel's stripe width and chunk

@@ -90,7 +90,8 @@ struct hk_ctx {
   uint32_t *A = nullptr;
   uint32_t *Aexp = nullptr;  // Karatsuba expansion of A (levels > 0)
   KarLayout kl{};
-  int kar_levels = 2;
+  int kar_levels = -1;       // Karatsuba levels of the factor update (-1: chosen per window)
+  int lv_W = -1, lv_auto = 0;  // cached automatic choice for window lv_W
   int update_path = 0;       // 0: IMAD product scanning, 1: INT8 mma.sync
   bool use_graph = false;    // capture each factorisation in a CUDA graph
   cudaStream_t cap_stream = nullptr;  // capture stream when `stream` is a default stream
@@ -488,12 +489,24 @@ __global__ void k_col_grid(int N, const long long *colU, int W, long long *colG)
 // one attempt of the blocked factorisation with window width c->W
 int factor_enqueue(hk_ctx *c, const Sched &sc, int r_start);
 
+// Karatsuba depth of the factor update for the current window: the option's
+// value, or the depth of least modelled update cost for W
+int factor_levels(hk_ctx *c) {
+  if (c->update_path == 1) return 0;
+  if (c->kar_levels >= 0) return c->kar_levels;
+  if (c->lv_W != c->W) {
+    c->lv_auto = choose_levels(c->W, KAR_GAP);
+    c->lv_W = c->W;
+  }
+  return c->lv_auto;
+}
+
 // one attempt of the factorisation from block row r_start (> 0: resume after a
 // window widening; rows above it are final and only re-aligned)
 int factor_attempt(hk_ctx *c, int r_start) {
   const int N = c->N, L = c->L, W = c->W, nb = c->nb;
   const size_t NT = (size_t)N * (N + 1) / 2;
-  const int levels = c->update_path == 1 ? 0 : c->kar_levels;
+  const int levels = factor_levels(c);
   kar_layout(W, levels, KAR_GAP, &c->kl);
   Sched sc;
   CK(sched_for(c, W, W, levels, &sc));
@@ -570,7 +583,7 @@ int factor_attempt(hk_ctx *c, int r_start) {
 // the factorisation's launch sequence (asynchronous on the context stream)
 int factor_enqueue(hk_ctx *c, const Sched &sc, int r_start) {
   const int N = c->N, L = c->L, W = c->W, nb = c->nb;
-  const int levels = c->update_path == 1 ? 0 : c->kar_levels;
+  const int levels = c->fac_levels;  // set by factor_attempt for this window
   CK(launch_col_tops(N, L, c->top_margin, c->mom, c->colU, c->st, c->stream));
   DBG(c, "col_tops", N, L);
   k_col_grid<<<(N + 127) / 128, 128, 0, c->stream>>>(N, c->colU, W, c->colG);
@@ -772,7 +785,9 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
       // Karatsuba on the factor's split points when the vector fits the
       // factor's window W: the solve contracts expanded entries like the factor
       const int Wv_need = std::max(4, round4((top - h + 31) / 32));
-      const bool kar_ok = c->fac_levels > 0 && c->Aexp && c->update_path == 0;
+      // (not at three levels: expanding each new entry into 27 pieces would
+      // lengthen the per-entry chain by more than the GEMV saves)
+      const bool kar_ok = c->fac_levels > 0 && c->fac_levels <= 2 && c->Aexp && c->update_path == 0;
       const int lv = kar_ok && Wv_need <= W ? c->fac_levels : 0;
       const int Wv = lv > 0 ? W : Wv_need;
       if (Wv > HK_MAX_WV) return HK_ERR_RANGE;  // no shared-memory tile could hold it
@@ -1059,15 +1074,19 @@ int hk_workspace_bytes(int N, int P, size_t *bytes) {
   const long long L = P / 32;
   const long long W = round4(L + (N + 128 + 31) / 32) + 64;  // one widening included
   const long long NT = (long long)N * (N + 1) / 2;
-  KarLayout kl;
-  kar_layout((int)W, 2, KAR_GAP, &kl);
+  long long kstride = 0;  // the widest Karatsuba expansion any depth may use
+  for (int lv = 1; lv <= MAX_KAR; lv++) {
+    KarLayout kl;
+    kar_layout((int)W, lv, KAR_GAP, &kl);
+    kstride = std::max<long long>(kstride, kl.stride);
+  }
   const long long C = 2 * W + 64;
   long long b = 0;
   b += (2LL * N) * (16 + 4 * L);          // moments
   b += 3LL * N * 8 + 4096;                // tops, grids, status
   b += NT * (16 + 4 * L);                 // R
   b += NT * (4 * W + 4);                  // aligned R
-  b += NT * 4LL * kl.stride;              // its Karatsuba expansion
+  b += NT * 4LL * kstride;                // its Karatsuba expansion
   b += (long long)N * (L + 2) * 4;        // reciprocals
   b += 16LL * N * C * 8;                  // column sums of one block
   b += 3LL * N * (16 + 4 * L) + 256LL * (16 + 4 * L);  // v, y, w, history
@@ -1193,7 +1212,7 @@ int hk_factor(hk_ctx *c, int *bad_row) {
   c->W = round4(c->L + (slack + 31) / 32);
   c->top_margin = 0;
   if (const char *e = getenv("HK_NB")) c->nb = std::max(1, atoi(e));  // panel block rows (tuning)
-  if (const char *e = getenv("HK_KARATSUBA")) c->kar_levels = std::min(2, std::max(0, atoi(e)));  // (tuning)
+  if (const char *e = getenv("HK_KARATSUBA")) c->kar_levels = std::min(MAX_KAR, std::max(-1, atoi(e)));  // (tuning)
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1260,8 +1279,8 @@ int hk_set_option(hk_ctx *c, int option, long long value) {
   switch (option) {
     case 0:  // update path
       return hk_set_update_path(c, (int)value);
-    case 1:  // Karatsuba levels of the factor update
-      if (value < 0 || value > 2) return HK_ERR_ARG;
+    case 1:  // Karatsuba levels of the factor update (-1: chosen per window)
+      if (value < -1 || value > MAX_KAR) return HK_ERR_ARG;
       c->kar_levels = (int)value;
       break;
     case 2:  // capture factorisations in CUDA graphs
@@ -1443,14 +1462,15 @@ int hk_get_stats(hk_ctx *c, int64_t *out, int n) {
   // the sub-contraction areas; W^2 without Karatsuba)
   SubProb sub[MAX_SUB];
   KarLayout kl;
-  kar_layout(c->W, c->update_path == 1 ? 0 : c->kar_levels, KAR_GAP, &kl);
+  const int lv = c->fac_levels >= 0 ? c->fac_levels : factor_levels(c);
+  kar_layout(c->W, lv, KAR_GAP, &kl);
   const int ns = kar_subprobs(kl, sub);
   int64_t per_mac = 0;
   for (int k = 0; k < ns; k++) per_mac += (int64_t)sub[k].wx * sub[k].wy;
   const int64_t v[9] = {c->launches,
                         c->W,
                         c->widenings,
-                        c->update_path == 1 ? 0 : c->kar_levels,
+                        lv,
                         per_mac,
                         c->eig_converged,
                         c->wv_max,

@@ -20,8 +20,9 @@ constexpr int UC_MAX = 13;
 constexpr int UPC = 36;        // default p-steps per unit (a multiple of the stripe width)
 constexpr int UNT = 256;       // compute threads per CTA
 constexpr int USTAGES = 4;     // shared-memory pipeline depth
-constexpr int MAX_SUB = 9;     // sub-contractions per launch (two Karatsuba levels)
-constexpr int MAX_TERMS = 4;   // result positions a sub-contraction is added to
+constexpr int MAX_KAR = 3;     // Karatsuba levels of the expansion
+constexpr int MAX_SUB = 27;    // sub-contractions per launch (3^levels)
+constexpr int MAX_TERMS = 8;   // result positions a sub-contraction is added to (2^levels)
 constexpr int MAX_XB = 64;     // blocks per output with their own operand window
 
 struct Unit {
@@ -41,15 +42,18 @@ struct SubProb {
   int tsign[MAX_TERMS];
 };
 
-// Karatsuba expansion of an aligned entry of W limbs (levels 0, 1 or 2):
+// Karatsuba expansion of an aligned entry of W limbs (levels 0 to 3):
 // pieces lo, hi, lo+hi (recursively), each stored in its own slot with zero
 // gaps of G limbs on both sides, so that one entry is one contiguous copy.
+// Piece k of the last level is the base-3 path (lo = 0, hi = 1, lo+hi = 2)
+// through the levels, most significant digit first.
 struct KarLayout {
   int levels;
   int W;
   int npieces;
   int m1;                  // level-1 split
   int m2[3];               // level-2 splits of lo, hi, lo+hi
+  int m3[9];               // level-3 splits of the nine level-2 pieces
   int off[MAX_SUB];        // slot offsets (limbs)
   int w[MAX_SUB];          // piece widths
   int G;                   // gap (limbs)
@@ -101,6 +105,7 @@ int build_units(const SubProb *sub, int nsub, int uc, int upc, Unit *host_out, i
 int operand_windows(const SubProb *sub, int nsub, const Unit *units, int n, int gap, int stride, int *xlo,
                     int *xlen);
 void choose_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc, int *upc);
+int choose_levels(int W, int gap);  // Karatsuba depth of least modelled update cost
 int colsum_width(const SubProb *sub, int nsub, int uc);
 cudaError_t launch_update(const UpdParams &p, cudaStream_t s);
 // INT8 tensor-core (mma.sync u8) form of the FACTOR update, plain entries

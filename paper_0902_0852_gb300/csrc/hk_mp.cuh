@@ -285,7 +285,8 @@ HK_DEV bool any_below(const uint32_t *x, int n, long long s, Red &r) {
       f |= (v != 0);
     }
   }
-  return cta_or<NT>(f, r) != 0;
+  (void)r;
+  return __syncthreads_or(f != 0) != 0;
 }
 
 // leading (up to) 64 bits of x as a double: x ~= return * 2^(*e); bl = bitlen(x)
@@ -383,20 +384,26 @@ HK_DEV bool recip(const uint32_t *D, int L, uint32_t *V, Work &w, NBufs &B) {
     shr<NT>(D, L, P - n2, Dk, nD);
     shl<NT>(X, nX, n2 - n, X0, nX0);
     __syncthreads();
-    mul<NT>(Dk, nD, X0, nX0, prod, w);  // nD + nX0 + 2 limbs
-    const int nE = nD + nX0 + 2;
-    // E = 2^(2 n2) - prod
+    // only the top bits of E = 2^(2 n2) - Dk X0 matter: corr = (X0 |E|) >> 2 n2
+    // with |E| ~ 2^(2 n2 - n); dropping the low se bits of E changes corr by
+    // less than one unit.  The product is formed from its columns >= D0 only:
+    // the dropped columns sum to less than 2^(32 D0 + 44) (at most 2^12
+    // products of 64 bits per column, P <= 32768), below 2^(se - 20), which
+    // moves |E| >> se by at most one more unit.
+    const long long se = max(0LL, n2 - 16);
+    const int D0 = max(0, (int)(se >> 5) - 2);
+    const int nPr = nD + nX0;
+    mul_cols<NT>(Dk, nD, X0, nX0, D0, nPr, w);
+    const int nE = nPr - D0 + 2;
+    // E / 2^(32 D0) = 2^(2 n2 - 32 D0) - columns
     for (int d = threadIdx.x; d < nE; d += NT) {
-      long long v = -(long long)prod[d];
-      if (d == (int)((2 * n2) >> 5)) v += 1LL << ((2 * n2) & 31);
+      long long v = -w.cs[d];
+      if (d == (int)((2 * n2) >> 5) - D0) v += 1LL << ((2 * n2) & 31);
       w.cs[d] = v;
     }
     __syncthreads();
     const bool eneg = resolve<NT>(w.cs, nE, E, *w.r);
-    // only the top bits of E matter: corr = (X0 |E|) >> 2 n2 with |E| ~ 2^(2 n2 - n);
-    // dropping the low se bits of E changes corr by less than one unit
-    const long long se = max(0LL, n2 - 16);
-    shr<NT>(E, nE + 2, se, corr, nE + 2);
+    shr<NT>(E, nE + 2, se - 32LL * D0, corr, nE + 2);
     __syncthreads();
     const long long eb = bitlen<NT>(corr, nE + 2, *w.r);
     const int nEm = max(1, limbs_for(eb));
@@ -490,18 +497,22 @@ HK_DEV bool isqrt(const uint32_t *A, int nA, uint32_t *X, int nX, bool *exact, W
     shl<NT>(Y, nY, n2 - n, Y0, nY0);
     __syncthreads();
     mul<NT>(Y0, nY0, Y0, nY0, t1, w);          // 2 nY0 + 2
-    mul<NT>(A2, nA2, t1, 2 * nY0, t2, w);      // nA2 + 2 nY0 + 2
-    const int nE = nA2 + 2 * nY0 + 2;
+    // corr = (Y0 |E|) >> (4 n2 + 1) with E = 2^(4 n2) - A2 Y0^2, |E| ~ 2^(4 n2 - n):
+    // keep only the bits of E from se up; the product A2 Y0^2 is formed from its
+    // columns >= D0 only (dropped part below 2^(32 D0 + 44) <= 2^(se - 20), as in recip)
+    const long long se = max(0LL, 3 * n2 - 16);
+    const int D0 = max(0, (int)(se >> 5) - 2);
+    const int nPr = nA2 + 2 * nY0;
+    mul_cols<NT>(A2, nA2, t1, 2 * nY0, D0, nPr, w);
+    const int nE = nPr - D0 + 2;
     for (int d = threadIdx.x; d < nE; d += NT) {
-      long long v = -(long long)t2[d];
-      if (d == (int)((4 * n2) >> 5)) v += 1LL << ((4 * n2) & 31);
+      long long v = -w.cs[d];
+      if (d == (int)((4 * n2) >> 5) - D0) v += 1LL << ((4 * n2) & 31);
       w.cs[d] = v;
     }
     __syncthreads();
     const bool eneg = resolve<NT>(w.cs, nE, t3, *w.r);
-    // corr = (Y0 |E|) >> (4 n2 + 1) with |E| ~ 2^(4 n2 - n): keep only the top bits of E
-    const long long se = max(0LL, 3 * n2 - 16);
-    shr<NT>(t3, nE + 2, se, t2, nE + 2);
+    shr<NT>(t3, nE + 2, se - 32LL * D0, t2, nE + 2);
     __syncthreads();
     const long long eb = bitlen<NT>(t2, nE + 2, *w.r);
     const int nEm = max(1, limbs_for(eb));
@@ -512,10 +523,16 @@ HK_DEV bool isqrt(const uint32_t *A, int nA, uint32_t *X, int nX, bool *exact, W
     nY = nY0 + 1;
     n = n2;
   }
-  // X ~ A * Y / 2^(2m)
-  mul<NT>(A, nA, Y, nY, t1, w);
-  shr<NT>(t1, nA + nY + 2, 2 * m, X, nX);
-  __syncthreads();
+  // X ~ A * Y / 2^(2m), from the product's columns >= D1 (the dropped part,
+  // below 2^(32 D1 + 44) <= 2^(2m - 20), moves X by at most one unit; the
+  // exact correction below settles X)
+  {
+    const int D1 = max(0, (int)((2 * m) >> 5) - 2);
+    mul_cols<NT>(A, nA, Y, nY, D1, nA + nY, w);
+    normalize<NT>(w.cs, nA + nY - D1, t1, *w.r);
+    shr<NT>(t1, nA + nY - D1 + 2, 2 * m - 32LL * D1, X, nX);
+    __syncthreads();
+  }
   bool ok = false;
   for (int it = 0; it < 8 && !ok; it++) {
     // rem = A - X^2

@@ -71,8 +71,10 @@ HK_DEV mp::Work swork(SSmem &s) {
 template <int NT>
 HK_DEV int form_exact_s(SSmem &s, const long long *colrow, int C, int32_t sv, long long ev,
                         const uint32_t *vl, int L, long long G, DevStatus *st, int *nZ_out) {
-  bool vz = true;
-  for (int l = 0; l < L; l++) vz &= (vl[l] == 0);
+  // v == 0? (each thread tests a strided part of the limbs; one barrier)
+  uint32_t nzl = 0;
+  for (int l = threadIdx.x; l < L; l += NT) nzl |= vl[l];
+  const bool vz = __syncthreads_or(nzl != 0) == 0;
   long long sh = ev - G;
   if (vz) sh = 0;
   if (sh < 0) {
@@ -273,8 +275,9 @@ __global__ void __launch_bounds__(NT) k_solve_block(SolveParams p, const uint32_
     if (p.nosum) G = p.rhs.exp[i];
     const long long *colrow = p.colsum + (long long)(i - p.r0) * p.C;
     const uint32_t *vl = p.rhs.limbs + (long long)i * L;
-    bool vz = true;
-    for (int l = 0; l < L; l++) vz &= (vl[l] == 0);
+    uint32_t nzl = 0;
+    for (int l = threadIdx.x; l < L; l += NT) nzl |= vl[l];
+    const bool vz = __syncthreads_or(nzl != 0) == 0;
     long long sh0 = p.rhs.exp[i] - G;
     if (vz) sh0 = 0;
     if (sh0 < 0) {

@@ -385,28 +385,27 @@ cudaError_t allow_dynamic_smem(const void *fn) {
 
 void kar_layout(int W, int levels, int gap, KarLayout *kl) {
   KarLayout k{};
+  levels = std::max(0, std::min(levels, MAX_KAR));
   k.levels = levels;
   k.W = W;
   k.G = ((gap + 3) / 4) * 4;
-  int w[MAX_SUB];
-  int n = 0;
-  if (levels <= 0) {
-    w[n++] = W;
-  } else {
-    k.m1 = (W + 1) / 2;
-    const int l1[3] = {k.m1, W - k.m1, std::max(k.m1, W - k.m1) + 1};
-    if (levels == 1) {
-      for (int u = 0; u < 3; u++) w[n++] = l1[u];
-    } else {
-      for (int u = 0; u < 3; u++) {
-        const int m2 = (l1[u] + 1) / 2;
-        k.m2[u] = m2;
-        w[n++] = m2;
-        w[n++] = l1[u] - m2;
-        w[n++] = std::max(m2, l1[u] - m2) + 1;
-      }
+  // widths level by level: piece u of a level splits at (w_u + 1) / 2 into
+  // pieces 3u (lo), 3u + 1 (hi) and 3u + 2 (lo + hi, one limb wider)
+  std::vector<int> w{W};
+  for (int lv = 1; lv <= levels; lv++) {
+    std::vector<int> nw;
+    for (size_t u = 0; u < w.size(); u++) {
+      const int m = (w[u] + 1) / 2;
+      if (lv == 1) k.m1 = m;
+      if (lv == 2) k.m2[u] = m;
+      if (lv == 3) k.m3[u] = m;
+      nw.push_back(m);
+      nw.push_back(w[u] - m);
+      nw.push_back(std::max(m, w[u] - m) + 1);
     }
+    w.swap(nw);
   }
+  const int n = (int)w.size();
   k.npieces = n;
   int off = k.G;
   for (int i = 0; i < n; i++) {
@@ -455,27 +454,32 @@ int kar_subprobs(const KarLayout &kl, SubProb *sub) {
     SubProb s{};
     s.xoff = s.yoff = kl.off[i];
     s.wx = s.wy = kl.w[i];
-    int o1[2], s1[2];
-    if (kl.levels == 1) {
-      const int n1 = coef(i, kl.m1, o1, s1);
-      for (int a = 0; a < n1; a++) {
-        s.toff[a] = o1[a];
-        s.tsign[a] = s1[a];
-      }
-      s.nterm = n1;
-    } else {
-      const int u = i / 3, v = i % 3;
-      int o2[2], s2[2];
-      const int n1 = coef(u, kl.m1, o1, s1);
-      const int n2 = coef(v, kl.m2[u], o2, s2);
-      int n = 0;
-      for (int a = 0; a < n1; a++)
-        for (int b = 0; b < n2; b++) {
-          s.toff[n] = o1[a] + o2[b];
-          s.tsign[n] = s1[a] * s2[b];
+    // the terms multiply out level by level: digit d_l of the piece's path
+    // picks the (offset, sign) list of its split at that level
+    s.nterm = 1;
+    s.toff[0] = 0;
+    s.tsign[0] = 1;
+    int parent = 0;  // index of the piece's ancestor within its level
+    for (int lv = 1; lv <= kl.levels; lv++) {
+      int div = 1;
+      for (int r = lv; r < kl.levels; r++) div *= 3;
+      const int digit = (i / div) % 3;
+      const int m = lv == 1 ? kl.m1 : (lv == 2 ? kl.m2[parent] : kl.m3[parent]);
+      int o[2], sg[2];
+      const int nc = coef(digit, m, o, sg);
+      int toff[MAX_TERMS], tsign[MAX_TERMS], n = 0;
+      for (int a = 0; a < s.nterm; a++)
+        for (int b = 0; b < nc; b++) {
+          toff[n] = s.toff[a] + o[b];
+          tsign[n] = s.tsign[a] * sg[b];
           n++;
         }
       s.nterm = n;
+      for (int a = 0; a < n; a++) {
+        s.toff[a] = toff[a];
+        s.tsign[a] = tsign[a];
+      }
+      parent = 3 * parent + digit;
     }
     sub[i] = s;
   }
@@ -542,31 +546,36 @@ int operand_windows(const SubProb *sub, int nsub, const Unit *units, int n, int 
   return maxlen;
 }
 
+// Modelled cost of a schedule: thread-products per t including the idle
+// threads of the last block, plus a per-unit cost (window load, stage
+// bookkeeping) in slots per stripe column, over the relative limb-product
+// slot rate of the stripe width.  Rates and unit cost are fitted to
+// factorisation timings on GB300 (N = 1000, W = 804, two Karatsuba levels,
+// seven (stripe, chunk) schedules).
+static const int kUcs[3] = {7, 9, 11};
+static const double kSpeed[3] = {41.7, 45.9, 45.1};
+static double schedule_cost(const SubProb *sub, int nsub, int ui, int upc) {
+  const int uc = kUcs[ui];
+  const int n = build_units(sub, nsub, uc, upc, nullptr, 0);
+  const int blocks = (n + UNT - 1) / UNT;
+  return ((double)blocks * UNT * upc * uc + (double)n * 1.75 * uc) / kSpeed[ui];
+}
+
 // Schedule: stripe width and chunk length (a multiple of it, at most upc_cap)
-// with the fewest thread-products per t including idle threads of the last
-// block and a per-unit window reload; HK_UC / HK_UPC override (tuning runs).
-void choose_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc_out, int *upc_out) {
+// of least modelled cost; chunks of one stripe width measured slower than the
+// model says, so chunks start at two.  HK_UC / HK_UPC override (tuning runs).
+static double best_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc_out, int *upc_out) {
   int uc_force = 0, upc_force = 0;
   if (const char *e = getenv("HK_UC")) uc_force = atoi(e);
   if (const char *e = getenv("HK_UPC")) upc_force = atoi(e);
-  // relative limb-product slot rates by stripe width and the per-unit cost
-  // (window load, stage bookkeeping) in slots per stripe column, fitted to
-  // factorisation timings on GB300 (N = 1000, W = 804, two Karatsuba levels,
-  // seven (stripe, chunk) schedules); chunks of one stripe width measured
-  // slower than the model says, so chunks start at two
-  const int ucs[3] = {7, 9, 11};
-  const double speed[3] = {41.7, 45.9, 45.1};
-  const double unit_cost = 1.75;
   int best_uc = UC, best_upc = 4 * UC;
   double best = 1e300;
   for (int ui = 0; ui < 3; ui++) {
-    const int uc = ucs[ui];
+    const int uc = kUcs[ui];
     if (uc_force && uc != uc_force) continue;
     for (int upc = 2 * uc; upc <= 8 * uc && upc <= upc_cap; upc += uc) {
       if (upc_force && upc != upc_force) continue;
-      const int n = build_units(sub, nsub, uc, upc, nullptr, 0);
-      const int blocks = (n + UNT - 1) / UNT;
-      const double cost = ((double)blocks * UNT * upc * uc + (double)n * unit_cost * uc) / speed[ui];
+      const double cost = schedule_cost(sub, nsub, ui, upc);
       if (cost < best) {
         best = cost;
         best_uc = uc;
@@ -576,6 +585,33 @@ void choose_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc_out, int
   }
   *uc_out = best_uc;
   *upc_out = best_upc;
+  return best;
+}
+
+void choose_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc_out, int *upc_out) {
+  best_schedule(sub, nsub, upc_cap, uc_out, upc_out);
+}
+
+// Karatsuba depth for a window of W limbs: the level count whose best
+// schedule has the least modelled cost (the model of choose_schedule, which
+// counts every thread slot of the unit grid, so narrow pieces pay for their
+// idle slots and per-unit overhead).
+int choose_levels(int W, int gap) {
+  int best_lv = 0;
+  double best = 1e300;
+  for (int lv = 0; lv <= MAX_KAR; lv++) {
+    KarLayout kl;
+    kar_layout(W, lv, gap, &kl);
+    SubProb sub[MAX_SUB];
+    const int nsub = kar_subprobs(kl, sub);
+    int uc = 0, upc = 0;
+    const double cost = best_schedule(sub, nsub, lv > 0 ? kl.G - 11 : 8 * UC_MAX, &uc, &upc);
+    if (cost < best * 0.98) {  // a deeper level must win by 2% (more expansion work per entry)
+      best = cost;
+      best_lv = lv;
+    }
+  }
+  return best_lv;
 }
 
 namespace {

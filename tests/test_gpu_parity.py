@@ -203,6 +203,34 @@ def test_solve_paths_bit_identical(hk, monkeypatch, fuse):
     assert hist == hist_o
 
 
+@pytest.mark.parametrize("N,beta,P", [(40, (7, 4), 2048), (24, (3, 4), 8192)])
+def test_karatsuba_depths_bit_identical(hk, N, beta, P):
+    """The factor update contracts Karatsuba pieces of one to three levels (27
+    sub-contractions at three, each added at up to eight offsets); the
+    identity is exact, so R and the inverse-iteration history (whose solves
+    expand the vector with the same split points) equal the oracle's at every
+    depth, and the automatic choice (-1) is one of them."""
+    m = inputs.moments(N, beta, P)
+    Ro = oracle.cholesky(m, N, P)
+    _, hist_o, _ = oracle.inverse_iteration(Ro, P, 4)
+    seen = set()
+    for lv in (-1, 0, 1, 2, 3):
+        with hk.Hankel(0) as h:
+            h.set_option(hk.HK_OPT_KARATSUBA, lv)
+            h.load(N, beta, P, m)
+            h.factor()
+            R = h.R()
+            lam, used = h.smallest_eig(4)
+            hist = h.history(4)
+            st = h.stats()
+        assert R == Ro, lv
+        assert hist == hist_o, lv
+        if lv >= 0:
+            assert st["karatsuba_levels"] == lv
+        seen.add(st["karatsuba_levels"])
+    assert len(seen) == 4
+
+
 # Slack 0 fails in the first block (a restart).  L = P/32 = 15 leaves exactly
 # one limb (32 bits) of slack after W is rounded up to a multiple of 4; for
 # beta = 3 and 4 the first row's entries spread less than that (at most 18 and
