@@ -317,6 +317,9 @@ def main():
         "time_to_lambda_s": t_dev / args.steps, "iters_used": used, "lambda_min": lam_str,
         "lambda_min_table3": "1.0892e-52" if (N, P) == (1000, 24576) else None,
         "factor_ms": fac_ms / args.steps, "inverse_iteration_ms": eig_ms / args.steps,
+        # per-phase device time (CUDA events around each launch group): update
+        # kernels of the factor, its diagonal/row kernels, and the solves
+        "phases_ms": {k: sum(r[2][k] for r in recs) / args.steps for k in ("update_ms", "panel_ms", "solve_ms")},
         "factor_macs_per_s": (N - 1) * N * (N + 1) / 6 / (fac_ms / args.steps / 1e3),
         "limb_products_per_s_factor": limbprod / args.steps / (fac_ms / args.steps / 1e3),
         "e2e": {"value": macs_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -519,7 +519,7 @@ int factor_attempt(hk_ctx *c, int r_start) {
     c->res_N = c->res_L = 0;
     CK(alloc_mp(c, c->res_arena, &c->R, NT, L));
     CK(alloc(c, c->res_arena, &c->Asign, NT));
-    CK(alloc(c, c->res_arena, &c->recip, (size_t)N * (L + 2)));
+    CK(alloc(c, c->res_arena, &c->recip, (size_t)N * recip_limbs(L)));
     c->res_N = N;
     c->res_L = L;
   }
@@ -1087,7 +1087,7 @@ int hk_workspace_bytes(int N, int P, size_t *bytes) {
   b += NT * (16 + 4 * L);                 // R
   b += NT * (4 * W + 4);                  // aligned R
   b += NT * 4LL * kstride;                // its Karatsuba expansion
-  b += (long long)N * (L + 2) * 4;        // reciprocals
+  b += (long long)N * recip_limbs((int)L) * 4;  // reciprocals
   b += 16LL * N * C * 8;                  // column sums of one block
   b += 3LL * N * (16 + 4 * L) + 256LL * (16 + 4 * L);  // v, y, w, history
   const long long Wv = 2 * W + (long long)N;  // vector window (generous)

@@ -24,6 +24,10 @@ constexpr int MAX_KAR = 3;     // Karatsuba levels of the expansion
 constexpr int MAX_SUB = 27;    // sub-contractions per launch (3^levels)
 constexpr int MAX_TERMS = 8;   // result positions a sub-contraction is added to (2^levels)
 constexpr int MAX_XB = 64;     // blocks per output with their own operand window
+// Guard bits of the stored row reciprocals floor(2^(2P+1+RECIP_EXTRA)/mant(R_ii)):
+// with them a correctly rounded division rarely needs its exact remainder.
+constexpr int RECIP_EXTRA = 64;
+__host__ __device__ inline int recip_limbs(int L) { return L + 2 + RECIP_EXTRA / 32; }
 
 struct Unit {
   int d0;  // first column of the stripe, sub-contraction index in bits 24..31
@@ -122,7 +126,7 @@ struct PanelParams {
   MpArr R;                 // R in floating form (packed)
   uint32_t *A;             // aligned entries (packed), W limbs
   int32_t *Asign;
-  uint32_t *recip;         // [N][L+2] floor(2^(2P+1)/mant(R_ii))
+  uint32_t *recip;         // [N][recip_limbs(L)] floor(2^(2P+1+RECIP_EXTRA)/mant(R_ii))
   const long long *colsum; // [block outputs][C]
   int r0;                  // block base row
   DevStatus *st;

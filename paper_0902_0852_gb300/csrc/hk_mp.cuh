@@ -361,11 +361,13 @@ HK_DEV bool lincomb(const uint32_t *x, int nx, int sa, const uint32_t *y, int ny
 
 HK_DEV int limbs_for(long long bits) { return (int)((bits + 31) >> 5); }
 
-// V[0..L+2) = floor(2^(2P+1) / D) for D[0..L) with its top bit set, P = 32 L.
+// V[0..L+2+extra/32) = floor(2^(2P+1+extra) / D) for D[0..L) with its top bit
+// set, P = 32 L, extra a multiple of 32 (guard bits for div_rne's fast path).
 // Returns false when the exact correction did not settle (never expected).
 template <int NT>
-HK_DEV bool recip(const uint32_t *D, int L, uint32_t *V, Work &w, NBufs &B) {
+HK_DEV bool recip(const uint32_t *D, int L, uint32_t *V, Work &w, NBufs &B, int extra = 0) {
   const long long P = 32LL * L;
+  const long long P2 = P + extra;  // Newton target: X ~ 2^(n + P) / D at precision n
   uint32_t *X = B.a, *X0 = B.b, *Dk = B.c, *prod = B.d, *E = B.e, *corr = B.f;
   // seed: n = 32, X = floor((2^64 - 1) / top32(D)) ~ 2^64 / D32
   long long n = 32;
@@ -378,10 +380,14 @@ HK_DEV bool recip(const uint32_t *D, int L, uint32_t *V, Work &w, NBufs &B) {
   }
   int nX = 3;
   __syncthreads();
-  while (n < P) {
-    const long long n2 = min(2 * n - 8, P);
+  while (n < P2) {
+    const long long n2 = min(2 * n - 8, P2);
     const int nD = limbs_for(n2), nX0 = limbs_for(n2 + 3);
-    shr<NT>(D, L, P - n2, Dk, nD);
+    // Dk = D 2^(n2 - P): its top n2 bits (exactly D shifted up past P)
+    if (n2 <= P)
+      shr<NT>(D, L, P - n2, Dk, nD);
+    else
+      shl<NT>(D, L, n2 - P, Dk, nD);
     shl<NT>(X, nX, n2 - n, X0, nX0);
     __syncthreads();
     // only the top bits of E = 2^(2 n2) - Dk X0 matter: corr = (X0 |E|) >> 2 n2
@@ -415,18 +421,19 @@ HK_DEV bool recip(const uint32_t *D, int L, uint32_t *V, Work &w, NBufs &B) {
     nX = nX0 + 1;
     n = n2;
   }
-  // V0 = 2X ~ 2^(2P+1)/D ; exact correction
-  const int nV = L + 2;
+  // V0 = 2X ~ 2^(2P+1+extra)/D ; exact correction
+  const int nV = L + 2 + extra / 32;
+  const long long E2 = 2 * P + 1 + extra;
   shl<NT>(X, nX, 1, X0, nV);
   __syncthreads();
   bool ok = false;
   for (int it = 0; it < 6 && !ok; it++) {
-    // rem = 2^(2P+1) - D*V0
+    // rem = 2^E2 - D*V0
     mul<NT>(D, L, X0, nV, prod, w);
     const int nR = L + nV + 2;
     for (int d = threadIdx.x; d < nR; d += NT) {
       long long v = -(long long)prod[d];
-      if (d == (int)((2 * P + 1) >> 5)) v += 1LL << ((2 * P + 1) & 31);
+      if (d == (int)(E2 >> 5)) v += 1LL << (E2 & 31);
       w.cs[d] = v;
     }
     __syncthreads();
@@ -596,31 +603,65 @@ HK_DEV Rounded sqrt_rne(const uint32_t *s, int L, long long e, uint32_t *mant, W
   return round_rne<NT>(big, nX + 3, (e2 - 2 * j) / 2 - 1, L, mant, w);
 }
 
-// mant, exponent of RNE_P(|num| 2^ne / (den 2^de)) where V = floor(2^(2P+1)/den).
-// num, den: normalised P-bit mantissas.  big: capacity >= 2L + 16.
-// Q = floor(num 2^(P+1) / den) (P+1 or P+2 bits) comes from the columns >= L-2
-// of num * V only: the dropped columns sum to less than (L-2) 2^(32(L-1)) <
-// 2^(32L), one unit of Q, and the Barrett estimate is at most one unit low, so
-// Q0 <= Q <= Q0 + 2.  The
-// remainder num 2^(P+1) - Q0 den lies in [0, 3 den) and is computed exactly
-// from the low L+3 limbs of Q0 * den; the correction then raises Q0 to Q.
+// mant, exponent of RNE_P(|num| 2^ne / (den 2^de)) where V = floor(2^(2P+1+vx)/den)
+// (L + 2 + vx/32 limbs, vx a multiple of 32).  num, den: normalised P-bit
+// mantissas.  big: capacity >= 2L + 16; q: L + 4 + vx/32.
+// Q = floor(num 2^(P+1+vx) / den) (P+1+vx or P+2+vx bits) comes from the
+// columns >= L-2 of num * V only: the dropped columns sum to less than
+// (L-2) 2^(32(L-1)) < 2^(32L), one unit of Q, and the Barrett estimate is at
+// most one unit low, so Q0 <= Q <= Q0 + 2.
+// Fast path (vx > 0): when the k = bitlen(Q0) - P - 1 >= vx bits of Q0 below
+// its guard bit hold a value T with 1 <= T <= 2^k - 3, adding up to 2 carries
+// into neither the guard bit nor the mantissa and leaves the low bits nonzero:
+// RNE_P(Q) = RNE_P(2 Q0 + 1) with the sticky bit set, no remainder needed.
+// Otherwise (exact or near-exact quotients) the remainder
+// num 2^(P+1+vx) - Q0 den lies in [0, 3 den) and is computed exactly from the
+// low L+3 limbs of Q0 * den; the correction then raises Q0 to Q.
 template <int NT>
 HK_DEV Rounded div_rne(const uint32_t *num, long long ne, const uint32_t *den, long long de,
                        const uint32_t *V, int L, uint32_t *mant, Work &w, uint32_t *big,
-                       uint32_t *q, bool *ok) {
+                       uint32_t *q, bool *ok, int vx = 0) {
   const long long P = 32LL * L;
-  const int nQ = L + 3;
+  const int nV = L + 2 + vx / 32;
+  const int nQ = L + 3 + vx / 32;
   // high columns of num * V: value sum_{d >= L-2} col_d 2^(32 d)
-  const int dlo = max(0, L - 2), dhi = 2 * L + 2;
-  mul_cols<NT>(num, L, V, L + 2, dlo, dhi, w);
+  const int dlo = max(0, L - 2), dhi = L + nV;
+  mul_cols<NT>(num, L, V, nV, dlo, dhi, w);
   normalize<NT>(w.cs, dhi - dlo, big, *w.r);  // big = that sum / 2^(32 dlo)
   // Q0 = floor(sum / 2^P)
   shr<NT>(big, dhi - dlo + 2, 32LL * (L - dlo), q, nQ);
   __syncthreads();
-  // rem = num 2^(P+1) - Q0 den  mod 2^(32 nR), exact since 0 <= rem < 3 den
+  if (vx > 0) {
+    if (threadIdx.x == 0) {
+      int top = nQ - 1;
+      while (top > 0 && q[top] == 0) top--;
+      const long long b = 32LL * top + 32 - __clz(q[top]);
+      const int k = (int)(b - P - 1);  // bits below the guard bit
+      const int kq = k >> 5, kr = k & 31;
+      const uint32_t mask = kr ? (1u << kr) - 1u : 0u;
+      bool zero = (q[kq] & mask) == 0, ones = (q[kq] & mask) == mask;
+      for (int l = 0; l < kq; l++) {
+        zero &= q[l] == 0;
+        ones &= (l == 0 ? (q[0] | 1u) : q[l]) == 0xffffffffu;
+      }
+      w.r->f[32] = (k >= vx && !zero && !ones) ? 1u : 0u;
+    }
+    __syncthreads();
+    const bool fast = w.r->f[32] != 0;
+    __syncthreads();
+    if (fast) {
+      // 2 Q0 + 1 (a shift and a set bit: no carries)
+      for (int d = threadIdx.x; d < nQ + 1; d += NT)
+        big[d] = (limb_at(q, nQ, d) << 1) | (d == 0 ? 1u : (limb_at(q, nQ, d - 1) >> 31));
+      __syncthreads();
+      *ok = true;
+      return round_rne<NT>(big, nQ + 1, ne - de - P - 2 - vx, L, mant, w);
+    }
+  }
+  // rem = num 2^(P+1+vx) - Q0 den  mod 2^(32 nR), exact since 0 <= rem < 3 den
   const int nR = L + 3;
   mul_cols<NT>(q, nQ, den, L, 0, nR, w);
-  const long long pos = P + 1;
+  const long long pos = P + 1 + vx;
   for (int d = threadIdx.x; d < nR; d += NT) {
     const uint32_t a = limb_at(num, L, d - (int)(pos >> 5));
     const uint32_t b = limb_at(num, L, d - (int)(pos >> 5) - 1);
@@ -650,12 +691,12 @@ HK_DEV Rounded div_rne(const uint32_t *num, long long ne, const uint32_t *den, l
     }
   }
   *ok = done;
-  // Q = Q0 + adj; result value (2Q + sticky) 2^(ne - de - P - 2)
+  // Q = Q0 + adj; result value (2Q + sticky) 2^(ne - de - P - 2 - vx)
   for (int d = threadIdx.x; d < nQ + 1; d += NT)
     w.cs[d] = 2LL * limb_at(q, nQ, d) + (d == 0 ? 2LL * adj + (sticky ? 1 : 0) : 0);
   __syncthreads();
   normalize<NT>(w.cs, nQ + 1, big, *w.r);
-  return round_rne<NT>(big, nQ + 3, ne - de - P - 2, L, mant, w);
+  return round_rne<NT>(big, nQ + 3, ne - de - P - 2 - vx, L, mant, w);
 }
 
 }  // namespace mp

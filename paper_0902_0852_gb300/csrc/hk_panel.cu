@@ -192,8 +192,8 @@ __global__ void __launch_bounds__(NT) k_diag(PanelParams p, int i) {
   if (p.kl.levels > 0)
     expand_entry<NT>(p.A + idx * p.W, p.kl, p.Aexp + idx * p.kl.stride, s.cs, s.Z, s.big, *s.red);
   __syncthreads();
-  ok = mp::recip<NT>(s.rm, L, s.V, w, B);
-  for (int l = threadIdx.x; l < L + 2; l += NT) p.recip[(long long)i * (L + 2) + l] = s.V[l];
+  ok = mp::recip<NT>(s.rm, L, s.V, w, B, RECIP_EXTRA);
+  for (int l = threadIdx.x; l < recip_limbs(L); l += NT) p.recip[(long long)i * recip_limbs(L) + l] = s.V[l];
   if (threadIdx.x == 0 && !ok) atomicAdd(&p.st->timeout, 1);
   (void)P;
 }
@@ -244,10 +244,10 @@ __global__ void __launch_bounds__(NT) k_offdiag(PanelParams p, int i) {
     return;
   }
   for (int l = threadIdx.x; l < L; l += NT) s.rm[l] = p.R.limbs[iidx * L + l];
-  for (int l = threadIdx.x; l < L + 2; l += NT) s.V[l] = p.recip[(long long)i * (L + 2) + l];
+  for (int l = threadIdx.x; l < recip_limbs(L); l += NT) s.V[l] = p.recip[(long long)i * recip_limbs(L) + l];
   __syncthreads();
   bool ok = true;
-  const mp::Rounded Q = mp::div_rne<NT>(s.mant, S.exp, s.rm, p.R.exp[iidx], s.V, L, s.res, w, s.big, s.q, &ok);
+  const mp::Rounded Q = mp::div_rne<NT>(s.mant, S.exp, s.rm, p.R.exp[iidx], s.V, L, s.res, w, s.big, s.q, &ok, RECIP_EXTRA);
   for (int l = threadIdx.x; l < L; l += NT) p.R.limbs[idx * L + l] = s.res[l];
   if (threadIdx.x == 0) {
     p.R.sign[idx] = sgn < 0 ? 1 : 0;

@@ -38,9 +38,9 @@ __global__ void __launch_bounds__(NT_ST) k_selftest(int op, int L, const uint32_
     const mp::Rounded r = mp::sqrt_rne<NT_ST>(x, L, ex, out, w, B, big, xs, &ok);
     if (threadIdx.x == 0) *eo = r.exp;
   } else if (op == 3) {
-    ok = mp::recip<NT_ST>(y, L, V, w, B);
+    ok = mp::recip<NT_ST>(y, L, V, w, B, RECIP_EXTRA);
     bool ok2 = true;
-    const mp::Rounded r = mp::div_rne<NT_ST>(x, ex, y, ey, V, L, out, w, big, q, &ok2);
+    const mp::Rounded r = mp::div_rne<NT_ST>(x, ex, y, ey, V, L, out, w, big, q, &ok2, RECIP_EXTRA);
     ok = ok && ok2;
     if (threadIdx.x == 0) *eo = r.exp;
   } else if (op == 4) {

@@ -158,11 +158,11 @@ __global__ void __launch_bounds__(NT) k_solve_entry(SolveParams p, int i) {
   }
   const long long iidx = tri_idx(i, i, N);
   for (int l = threadIdx.x; l < L; l += NT) s.rm[l] = p.R.limbs[iidx * L + l];
-  for (int l = threadIdx.x; l < L + 2; l += NT) s.V[l] = p.recip[(long long)i * (L + 2) + l];
+  for (int l = threadIdx.x; l < recip_limbs(L); l += NT) s.V[l] = p.recip[(long long)i * recip_limbs(L) + l];
   __syncthreads();
   bool ok = true;
   const mp::Rounded Q =
-      mp::div_rne<NT>(s.mant, S.exp, s.rm, p.R.exp[iidx], s.V, L, s.res, w, s.big, s.q, &ok);
+      mp::div_rne<NT>(s.mant, S.exp, s.rm, p.R.exp[iidx], s.V, L, s.res, w, s.big, s.q, &ok, RECIP_EXTRA);
   for (int l = threadIdx.x; l < L; l += NT) outl[l] = s.res[l];
   if (threadIdx.x == 0) {
     p.out.sign[i] = sgn < 0 ? 1 : 0;
@@ -332,11 +332,11 @@ __global__ void __launch_bounds__(NT) k_solve_block(SolveParams p, const uint32_
     }
     const long long iidx = tri_idx(i, i, N);
     for (int l = threadIdx.x; l < L; l += NT) s.rm[l] = p.R.limbs[iidx * L + l];
-    for (int l = threadIdx.x; l < L + 2; l += NT) s.V[l] = p.recip[(long long)i * (L + 2) + l];
+    for (int l = threadIdx.x; l < recip_limbs(L); l += NT) s.V[l] = p.recip[(long long)i * recip_limbs(L) + l];
     __syncthreads();
     bool ok = true;
     const mp::Rounded Q =
-        mp::div_rne<NT>(s.mant, S.exp, s.rm, p.R.exp[iidx], s.V, L, s.res, w, s.big, s.q, &ok);
+        mp::div_rne<NT>(s.mant, S.exp, s.rm, p.R.exp[iidx], s.V, L, s.res, w, s.big, s.q, &ok, RECIP_EXTRA);
     for (int l = threadIdx.x; l < L; l += NT) outl[l] = s.res[l];
     if (threadIdx.x == 0) {
       p.out.sign[i] = sgn < 0 ? 1 : 0;
@@ -468,9 +468,9 @@ __global__ void __launch_bounds__(NT_LAM) k_lambda(int L, const long long *colsu
   mp::NBufs B;
   for (int t = 0; t < 6; t++) (&B.a)[t] = s.nb[t];
   B.cap = s.cap4;
-  bool ok = mp::recip<NT_LAM>(s.rm, L, s.V, w, B);
+  bool ok = mp::recip<NT_LAM>(s.rm, L, s.V, w, B, RECIP_EXTRA);
   bool ok2 = true;
-  const mp::Rounded Q = mp::div_rne<NT_LAM>(s.mant, VV.exp, s.rm, VW.exp, s.V, L, s.res, w, s.big, s.q, &ok2);
+  const mp::Rounded Q = mp::div_rne<NT_LAM>(s.mant, VV.exp, s.rm, VW.exp, s.V, L, s.res, w, s.big, s.q, &ok2, RECIP_EXTRA);
   for (int l = threadIdx.x; l < L; l += NT_LAM) lam.limbs[(long long)slot * L + l] = s.res[l];
   if (threadIdx.x == 0) {
     lam.sign[slot] = 0;
