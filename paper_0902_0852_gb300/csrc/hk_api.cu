@@ -783,11 +783,12 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
       }
       sp.nosum = have_known ? 0 : 1;
       // Karatsuba on the factor's split points when the vector fits the
-      // factor's window W: the solve contracts expanded entries like the factor
+      // factor's window W: the block's GEMV contracts the expanded R entries
+      // with the known vector entries, expanded for this block's grid in one
+      // parallel launch.  The in-block updates (one new entry at a time) use
+      // the plain aligned operands, so no expansion sits on the per-entry chain.
       const int Wv_need = std::max(4, round4((top - h + 31) / 32));
-      // (not at three levels: expanding each new entry into 27 pieces would
-      // lengthen the per-entry chain by more than the GEMV saves)
-      const bool kar_ok = c->fac_levels > 0 && c->fac_levels <= 2 && c->Aexp && c->update_path == 0;
+      const bool kar_ok = c->fac_levels > 0 && c->Aexp && c->update_path == 0;
       const int lv = kar_ok && Wv_need <= W ? c->fac_levels : 0;
       const int Wv = lv > 0 ? W : Wv_need;
       if (Wv > HK_MAX_WV) return HK_ERR_RANGE;  // no shared-memory tile could hold it
@@ -796,13 +797,15 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
         c->wv_sum += Wv;
         c->wv_count++;
       }
-      Sched sc;
+      Sched sc, sc0;  // GEMV schedule; plain schedule of the in-block updates
       CK(sched_for(c, W, Wv, lv, &sc));
-      const int Cs = sc.C;
+      sc0 = sc;
+      if (lv > 0) CK(sched_for(c, W, Wv, 0, &sc0));
+      const int Cs = std::max(sc.C, sc0.C);  // column-sum row width serving both
       int rc = ensure_vec(c, Wv, Cs, nbs, lv > 0 ? c->kl.stride : 0);
       if (rc) return rc;
       sp.kl = c->kl;
-      if (lv == 0) sp.kl.levels = 0;
+      sp.kl.levels = 0;  // solve entries write only their aligned form
       sp.vecAexp = c->vecAexp;
       sp.vecA = c->vecA;
       sp.vecAsign = c->vecAsign;
@@ -844,7 +847,21 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
       up.vy_len = lv > 0 ? (long long)c->vecAexp_cap : (long long)c->vec_cap;
       up.colsum_len = (long long)c->colsum_s_cap;
       fill_sched(up, sc);
+      up.C = Cs;
       up.st = c->st;
+      UpdParams upi = up;  // in-block updates
+      if (lv > 0) {
+        upi.A = c->A;
+        upi.astride = W;
+        upi.Vy = c->vecA;
+        upi.vstride = Wv;
+        upi.cx = W;
+        upi.cy = Wv;
+        upi.a_len = c->A_len;
+        upi.vy_len = (long long)c->vec_cap;
+        fill_sched(upi, sc0);
+        upi.C = Cs;
+      }
       const long long cta_per_out = (sc.n + UNT - 1) / UNT;
       const long long target = 6LL * sm_count(c) * 3;
       if (have_known) {
@@ -878,18 +895,18 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
         const bool more = back ? (i > B0) : (i + 1 < B1);
         if (more) {
           if (back) {
-            up.ra = B0;
-            up.rb = i;
+            upi.ra = B0;
+            upi.rb = i;
           } else {
-            up.ra = i + 1;
-            up.rb = B1;
+            upi.ra = i + 1;
+            upi.rb = B1;
           }
-          up.nout = up.rb - up.ra;
-          up.t0 = i;
-          up.t1 = i + 1;
-          up.tchunk = 1;
-          CK(launch_update(up, c->stream));
-          DBG(c, "gemv/dot update", up.ra, up.t0);
+          upi.nout = upi.rb - upi.ra;
+          upi.t0 = i;
+          upi.t1 = i + 1;
+          upi.tchunk = 1;
+          CK(launch_update(upi, c->stream));
+          DBG(c, "gemv/dot update", upi.ra, upi.t0);
           c->launches++;
         }
       }
