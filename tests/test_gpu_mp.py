@@ -73,6 +73,32 @@ def test_division_correctly_rounded(hk, L):
         assert got == want, (L, a, b)
 
 
+@pytest.mark.parametrize("L", [1, 2, 3, 64, 768])
+def test_division_exact_and_near_exact_quotients(hk, L):
+    """Exact quotients, which the guard-bit fast path must hand to the exact
+    remainder (num = den, a power-of-two divisor), and quotients next to exact
+    values (num = den * k cut back to P bits, and a unit of num either side),
+    against the oracle's correctly rounded division.  (An exact tie cannot
+    occur: its odd part would need P + 1 bits but divides num's odd part.)"""
+    rng = random.Random(400 + L)
+    P = 32 * L
+    cases = []
+    for _ in range(3):
+        den = _rand_bits(rng, P)
+        cases.append((den, den))                          # quotient exactly 1
+        cases.append((_rand_bits(rng, P), 1 << (P - 1)))  # power-of-two divisor
+        for k in (3, 5, 7):
+            num = den * k
+            num >>= num.bit_length() - P
+            cases += [(num, den), (num - 1, den), (num + 1, den)]
+    for a, b in cases:
+        if a.bit_length() != P or b.bit_length() != P:
+            continue
+        ea, eb = rng.randrange(-40, 40), rng.randrange(-40, 40)
+        got = hk.hk_selftest_mp(3, L, a, ex=ea, y=b, ey=eb)
+        assert got == H.mp_div((a, ea), (b, eb), P), (L, a, b)
+
+
 @pytest.mark.parametrize("L", [1, 2, 64, 256])
 def test_rounding_rne(hk, L):
     rng = random.Random(300 + L)
