@@ -266,6 +266,36 @@ int hk_mlp_train(float *params, float *m, float *v, float *grad, const float *x,
                  const float *w, int B, int steps, int step0, float lr, float beta1, float beta2,
                  float eps, float *loss_hist, void *work, size_t work_bytes, void *stream);
 
+/* Host-side plan of the exact update kernel for an accumulation window of W
+ * limbs: what hk_factor launches for that window when schedules are not
+ * autotuned (HK_OPT_AUTOTUNE 0, the default).  No GPU work, no device memory;
+ * for tests and tooling.  The plan expands every aligned entry a[0..W) into
+ * Karatsuba pieces (lo, hi, lo + hi of a split, recursively), contracts piece k
+ * of the X entries with piece k of the Y entries exactly, and adds that
+ * contraction to the result at each of its terms (offset in limbs, sign).
+ *   levels     Karatsuba depth 0..3, or -1 for the depth of least modelled
+ *              update cost (the hk_factor default)
+ *   info[9]    out: [0] depth, [1] pieces n, [2] expanded entry stride in
+ *              limbs, [3] zero gap between pieces (limbs), [4] stripe width
+ *              uc, [5] chunk length upc, [6] units, [7] blocks per output with
+ *              their own operand window (0: blocks stage whole entries), [8]
+ *              column-sum width C
+ *   splits[13] out (may be NULL): level-1 split m1, level-2 splits of the lo,
+ *              hi, lo+hi pieces, level-3 splits of the nine level-2 pieces
+ *              (unused levels 0)
+ *   pieces     out (may be NULL, 3 x 27 ints): per piece k < n its offset in
+ *              the expanded entry, width, number of terms
+ *   terms      out (may be NULL, 2 x 8 x 27 ints): term t of piece k at
+ *              [2(8k + t)] (offset in limbs) and [2(8k + t) + 1] (sign +-1)
+ *   units      out (may be NULL, 2 x ucap ints): unit u = (piece << 24 |
+ *              first result column of its stripe, first p of its chunk)
+ *   win        out (may be NULL, 2 x 64 ints): block b's operand window
+ *              (first limb, limbs) within the expanded entry
+ * Returns HK_ERR_ARG for W < 1, levels outside -1..3, a NULL info, or ucap
+ * below the unit count when units is given. */
+int hk_update_plan(int W, int levels, int64_t *info, int32_t *splits, int32_t *pieces, int32_t *terms,
+                   int32_t *units, int64_t ucap, int32_t *win);
+
 /* Load a trained predictor network into the context: params = HK_MLP_NPARAMS
  * host floats (layout above), scales = 10 host doubles: feature means and
  * standard deviations (2 + 2; features log2 N - 8 and log2 beta) and target

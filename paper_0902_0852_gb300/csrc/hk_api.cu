@@ -356,6 +356,51 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
   return ok && best < 1e30f;
 }
 
+// host part of a schedule (no device work): the sub-contractions of an update
+// of widths (Wx, Wy) -- the Karatsuba pieces of the factor shape when
+// levels > 0 (then Wx == Wy) -- and the longest chunk a unit may take
+struct SubPlan {
+  KarLayout kl;
+  SubProb sub[MAX_SUB];
+  int nsub;
+  int upc_cap;
+};
+
+void plan_subprobs(int Wx, int Wy, int levels, SubPlan *sp) {
+  *sp = SubPlan{};
+  sp->upc_cap = 8 * UC_MAX;
+  if (levels > 0) {
+    kar_layout(Wx, levels, KAR_GAP, &sp->kl);
+    sp->nsub = kar_subprobs(sp->kl, sp->sub);
+    sp->upc_cap = sp->kl.G - 11;  // a unit may read up to stripe + chunk limbs past its piece
+  } else {
+    sp->nsub = 1;
+    sp->sub[0] = SubProb{};
+    sp->sub[0].wx = Wx;
+    sp->sub[0].wy = Wy;
+    sp->sub[0].nterm = 1;
+    sp->sub[0].tsign[0] = 1;
+  }
+}
+
+// unit table, operand windows and column-sum width of schedule (uc, upc)
+void plan_units(const SubPlan &sp, int Wx, int Wy, int levels, int uc, int upc, Sched *sc, std::vector<Unit> *h) {
+  sc->uc = uc;
+  sc->upc = upc;
+  sc->nsub = sp.nsub;
+  for (int k = 0; k < sp.nsub; k++) sc->sub[k] = sp.sub[k];
+  sc->C = std::max(colsum_width(sp.sub, sp.nsub, uc), ((Wx + Wy + 8 + 3) / 4) * 4);
+  sc->n = build_units(sp.sub, sp.nsub, uc, upc, nullptr, 0);
+  h->assign(sc->n, Unit{0, 0});
+  build_units(sp.sub, sp.nsub, uc, upc, h->data(), sc->n);
+  sc->nxb = 0;
+  sc->maxlen = 0;
+  if (levels > 0) {
+    sc->maxlen = operand_windows(sp.sub, sp.nsub, h->data(), sc->n, sp.kl.G, sp.kl.stride, sc->xlo, sc->xlen);
+    if (sc->maxlen > 0) sc->nxb = (sc->n + UNT - 1) / UNT;
+  }
+}
+
 // schedule of an update launch: the Karatsuba-expanded factor update
 // (levels > 0) or a plain contraction of widths (Wx, Wy)
 cudaError_t sched_for(hk_ctx *c, int Wx, int Wy, int levels, Sched *out) {
@@ -365,22 +410,10 @@ cudaError_t sched_for(hk_ctx *c, int Wx, int Wy, int levels, Sched *out) {
     *out = it->second;
     return cudaSuccess;
   }
-  Sched sc{};
-  int upc_cap = 8 * UC_MAX;
-  if (levels > 0) {
-    KarLayout kl;
-    kar_layout(Wx, levels, KAR_GAP, &kl);
-    sc.nsub = kar_subprobs(kl, sc.sub);
-    upc_cap = kl.G - 11;  // a unit may read up to stripe + chunk limbs past its piece
-  } else {
-    sc.nsub = 1;
-    sc.sub[0] = SubProb{};
-    sc.sub[0].wx = Wx;
-    sc.sub[0].wy = Wy;
-    sc.sub[0].nterm = 1;
-    sc.sub[0].tsign[0] = 1;
-  }
-  choose_schedule(sc.sub, sc.nsub, upc_cap, &sc.uc, &sc.upc);
+  SubPlan sp;
+  plan_subprobs(Wx, Wy, levels, &sp);
+  int uc = 0, upc = 0;
+  choose_schedule(sp.sub, sp.nsub, sp.upc_cap, &uc, &upc);
   if (c->autotune && !c->ws && Wx == Wy) {
     // measured choice for factor-update shapes (cached for the process)
     const auto tkey = std::make_pair((long long)Wx, (long long)levels);
@@ -389,35 +422,24 @@ cudaError_t sched_for(hk_ctx *c, int Wx, int Wy, int levels, Sched *out) {
       std::lock_guard<std::mutex> lock(g_tune_mu);
       auto t = g_tune.find(tkey);
       if (t != g_tune.end()) {
-        sc.uc = t->second.first;
-        sc.upc = t->second.second;
+        uc = t->second.first;
+        upc = t->second.second;
         have = true;
       }
     }
     if (!have) {
-      KarLayout kl;
-      kar_layout(Wx, levels, KAR_GAP, &kl);
-      int uc = sc.uc, upc = sc.upc;
-      if (autotune_schedule(c, sc.sub, sc.nsub, levels > 0 ? kl.stride : Wx, upc_cap, &uc, &upc)) {
-        sc.uc = uc;
-        sc.upc = upc;
+      int tuc = uc, tupc = upc;
+      if (autotune_schedule(c, sp.sub, sp.nsub, levels > 0 ? sp.kl.stride : Wx, sp.upc_cap, &tuc, &tupc)) {
+        uc = tuc;
+        upc = tupc;
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune[tkey] = std::make_pair(uc, upc);
       }
     }
   }
-  sc.C = std::max(colsum_width(sc.sub, sc.nsub, sc.uc), ((Wx + Wy + 8 + 3) / 4) * 4);
-  sc.n = build_units(sc.sub, sc.nsub, sc.uc, sc.upc, nullptr, 0);
-  std::vector<Unit> h(sc.n);
-  build_units(sc.sub, sc.nsub, sc.uc, sc.upc, h.data(), sc.n);
-  sc.nxb = 0;
-  sc.maxlen = 0;
-  if (levels > 0) {
-    KarLayout kl;
-    kar_layout(Wx, levels, KAR_GAP, &kl);
-    sc.maxlen = operand_windows(sc.sub, sc.nsub, h.data(), sc.n, kl.G, kl.stride, sc.xlo, sc.xlen);
-    if (sc.maxlen > 0) sc.nxb = (sc.n + UNT - 1) / UNT;
-  }
+  Sched sc{};
+  std::vector<Unit> h;
+  plan_units(sp, Wx, Wy, levels, uc, upc, &sc, &h);
   cudaError_t e = alloc(c, c->base_arena, &sc.units, (size_t)sc.n);
   if (e != cudaSuccess) return e;
   // on the context's stream: a plain cudaMemcpy runs on the legacy default
@@ -1503,6 +1525,50 @@ int hk_selftest_mp(int op, int L, const uint32_t *x, int nx, int64_t ex, const u
   if (!x || !out || !eo || (ny > 0 && !y)) return HK_ERR_ARG;
   const int rc = hk::selftest_mp(op, L, x, nx, ex, y, ny, ey, out, eo);
   return rc == 0 ? HK_OK : (rc == 1 ? HK_ERR_ARG : HK_ERR_CUDA);
+}
+
+int hk_update_plan(int W, int levels, int64_t *info, int32_t *splits, int32_t *pieces, int32_t *terms,
+                   int32_t *units, int64_t ucap, int32_t *win) {
+  if (W < 1 || W > (1 << 20) || levels < -1 || levels > MAX_KAR || !info) return HK_ERR_ARG;
+  const int lv = levels < 0 ? choose_levels(W, KAR_GAP) : levels;
+  SubPlan sp;
+  plan_subprobs(W, W, lv, &sp);
+  int uc = 0, upc = 0;
+  choose_schedule(sp.sub, sp.nsub, sp.upc_cap, &uc, &upc);
+  Sched sc{};
+  std::vector<Unit> h;
+  plan_units(sp, W, W, lv, uc, upc, &sc, &h);
+  if (units && ucap < sc.n) return HK_ERR_ARG;
+  const int64_t v[9] = {lv, sc.nsub, lv > 0 ? sp.kl.stride : W, lv > 0 ? sp.kl.G : 0, uc, upc, sc.n, sc.nxb, sc.C};
+  for (int k = 0; k < 9; k++) info[k] = v[k];
+  if (splits) {
+    splits[0] = sp.kl.m1;
+    for (int k = 0; k < 3; k++) splits[1 + k] = sp.kl.m2[k];
+    for (int k = 0; k < 9; k++) splits[4 + k] = sp.kl.m3[k];
+  }
+  for (int k = 0; k < sc.nsub; k++) {
+    if (pieces) {
+      pieces[3 * k] = sc.sub[k].xoff;
+      pieces[3 * k + 1] = sc.sub[k].wx;
+      pieces[3 * k + 2] = sc.sub[k].nterm;
+    }
+    if (terms)
+      for (int t = 0; t < sc.sub[k].nterm; t++) {
+        terms[2 * (MAX_TERMS * k + t)] = sc.sub[k].toff[t];
+        terms[2 * (MAX_TERMS * k + t) + 1] = sc.sub[k].tsign[t];
+      }
+  }
+  if (units)
+    for (int u = 0; u < sc.n; u++) {
+      units[2 * u] = h[u].d0;
+      units[2 * u + 1] = h[u].p0;
+    }
+  if (win)
+    for (int b = 0; b < sc.nxb; b++) {
+      win[2 * b] = sc.xlo[b];
+      win[2 * b + 1] = sc.xlen[b];
+    }
+  return HK_OK;
 }
 
 int hk_set_predictor(hk_ctx *c, const float *params, const double *scales) {

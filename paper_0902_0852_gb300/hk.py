@@ -29,7 +29,7 @@ EXPORTS = [
     "hk_probe_int_peaks", "hk_mp_op_noalloc", "hk_set_update_path",
     "hk_set_option", "hk_batch_solve",
     "hk_mlp_workspace_bytes", "hk_mlp_forward", "hk_mlp_loss_grad", "hk_mlp_adam", "hk_mlp_train",
-    "hk_set_predictor", "hk_predict",
+    "hk_set_predictor", "hk_predict", "hk_update_plan",
 ]
 
 
@@ -84,6 +84,7 @@ def lib():
         L.hk_mlp_train.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, f32, f32, f32, f32, vp, vp, sz, vp]
         L.hk_set_predictor.argtypes = [vp, vp, vp]
         L.hk_predict.argtypes = [vp, i32, vp, vp, vp]
+        L.hk_update_plan.argtypes = [i32, i32, P64, P32, P32, P32, P32, i64, P32]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype if name in ("hk_destroy", "hk_strerror") else i32
         L.hk_mlp_workspace_bytes.restype = sz
@@ -433,6 +434,36 @@ def hk_mlp_train(params, m, v, grad, x, t, w, steps, step0, lr, work, loss_hist=
     _check(lib().hk_mlp_train(_dp(params), _dp(m), _dp(v), _dp(grad), _dp(x), _dp(t), _dp(w), x.shape[0], steps,
                               step0, lr, beta1, beta2, eps, _dp(loss_hist), _dp(work),
                               work.numel() * work.element_size(), _stream(stream)), "hk_mlp_train")
+
+
+def hk_update_plan(W, levels=-1, with_units=True):
+    """Host-side plan of the exact update for a window of W limbs (no GPU):
+    the Karatsuba depth, pieces (offset, width), their (offset, sign) terms,
+    split points, the (stripe, chunk) schedule, the unit table and the
+    per-block operand windows -- what hk_factor launches for that window."""
+    L = lib()
+    info = (ctypes.c_int64 * 9)()
+    splits = (ctypes.c_int32 * 13)()
+    pieces = (ctypes.c_int32 * (3 * 27))()
+    terms = (ctypes.c_int32 * (2 * 8 * 27))()
+    _check(L.hk_update_plan(W, levels, info, splits, pieces, terms, None, 0, None), "hk_update_plan")
+    n, nunits, nxb = info[1], info[6], info[7]
+    units = win = None
+    if with_units:
+        ub = (ctypes.c_int32 * (2 * nunits))()
+        wb = (ctypes.c_int32 * (2 * 64))()
+        _check(L.hk_update_plan(W, levels, info, None, None, None, ub, nunits, wb), "hk_update_plan")
+        units = [(ub[2 * u] >> 24, ub[2 * u] & 0xFFFFFF, ub[2 * u + 1]) for u in range(nunits)]
+        win = [(wb[2 * b], wb[2 * b + 1]) for b in range(nxb)]
+    return {
+        "levels": info[0], "npieces": n, "stride": info[2], "gap": info[3], "uc": info[4], "upc": info[5],
+        "nunits": nunits, "nxb": nxb, "C": info[8],
+        "m1": splits[0], "m2": list(splits[1:4]), "m3": list(splits[4:13]),
+        "pieces": [(pieces[3 * k], pieces[3 * k + 1]) for k in range(n)],
+        "terms": [[(terms[2 * (8 * k + t)], terms[2 * (8 * k + t) + 1]) for t in range(pieces[3 * k + 2])]
+                  for k in range(n)],
+        "units": units, "windows": win,
+    }
 
 
 def hk_set_predictor(ctx, params, x_mean, x_std, y_mean, y_std):
