@@ -191,9 +191,13 @@ def test_beta74_N4_worked_example():
             assert abs(recon - F(m[i + j])) <= Fraction(8, 2 ** P) * F(m[i + j])
 
 
-@pytest.mark.parametrize("beta", [(1, 1), (7, 4), (3, 4)])
-def test_local_residuals(beta):
-    P, N = 96, 14
+@pytest.mark.parametrize("beta,N,P", [((1, 1), 14, 96), ((7, 4), 14, 96), ((3, 4), 14, 96),
+                                      ((7, 4), 40, 384), ((3, 4), 40, 384), ((3, 2), 40, 384),
+                                      ((7, 4), 64, 2048)])
+def test_local_residuals(beta, N, P):
+    """Every entry of R is the once-rounded value of its exact defining sum
+    (within the bounds of one rounding), at the sizes of the device parity
+    cases with beta != 1, where no closed form is known."""
     m = inputs.moments(N, beta, P)
     R = H.cholesky(m, N, P)
     assert _residual_ok(m, R, P)
