@@ -8,7 +8,7 @@ Number format.  A P-bit float is a pair ``(n, e)`` of Python ints with value
 ``n * 2**e``; either ``n == 0 and e == 0`` or ``2**(P-1) <= |n| < 2**P``.
 Exponents are unbounded (no overflow, no subnormals).
 
-Readings of the paper taken here (each is listed in the design doc):
+Readings of the paper taken here:
 
 1. The paper computes an LDL^T determinant in GMP fixed point with K and K/2
    fractional bits (section "The LDL^T Determinant Algorithm").  This oracle
