@@ -220,7 +220,8 @@ def _mp_lambda_min(moments, N, prec):
 
 @pytest.mark.parametrize("beta,N,P,T", [((1, 1), 4, 256, 60), ((7, 4), 4, 256, 60),
                                         ((1, 1), 16, 640, 40), ((7, 4), 12, 512, 40),
-                                        ((3, 4), 10, 512, 40)])
+                                        ((3, 4), 10, 512, 40), ((7, 4), 32, 1024, 60),
+                                        ((1, 1), 32, 1536, 60), ((3, 4), 24, 1024, 60)])
 def test_lambda_vs_2P_eigensolve(beta, N, P, T):
     """Relative error of lambda_min against an independent dense symmetric
     eigensolve of the same (rounded-moment) matrix at 2P bits is <= 2^-128."""
