@@ -126,6 +126,19 @@ def sample_rows(N):
     return row0, min(N, row0 + ORACLE_ROWS)
 
 
+def reduce_over_ranks(t_dev, t_e2e, macs, macs_e2e, device):
+    """Whole-job figures of a replicas run (every rank solves its own
+    instance): the slowest rank's device and end-to-end times, and the MACs of
+    all ranks.  Collective over the default process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_dev, t_e2e], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    m = torch.tensor([macs, macs_e2e], device=device, dtype=torch.float64)
+    dist.all_reduce(m, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), float(m[0]), float(m[1])
+
+
 # ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
@@ -302,13 +315,7 @@ def main():
     macs = sum(step_macs(N, r[1]) for r in recs)
     macs_e2e = sum(step_macs(N, r[1]) for r in recs_e2e)
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_dev, t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev, t_e2e = float(t[0]), float(t[1])
-        m = torch.tensor([macs, macs_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(m, op=dist.ReduceOp.SUM)
-        macs, macs_e2e = float(m[0]), float(m[1])
+        t_dev, t_e2e, macs, macs_e2e = reduce_over_ranks(t_dev, t_e2e, macs, macs_e2e, "cuda")
     if rank != 0:
         h.close()
         return
