@@ -179,6 +179,51 @@ def _residual_ok(moments, R, P):
     return True
 
 
+def _audit(moments, R, P):
+    """Every rounding of R checked against its definition, exactly: from the
+    finished rows, the exact A_ij and S_ij = RNE(A_ij) (the exhaustive rational
+    rounding above, not the oracle's); R_ii against the squaring bounds of its
+    rounding interval (half an ulp above, half an ulp below -- a quarter at the
+    bottom of a binade -- ties to an even mantissa); R_ij against the rational
+    rounding of S_ij / R_ii."""
+    N = len(R)
+    for i in range(N):
+        rii = R[i][0]
+        for j in range(i, N):
+            A = F(moments[i + j]) - sum((F(R[t][i - t]) * F(R[t][j - t]) for t in range(i)), Fraction(0))
+            S = round_fraction(A, P)
+            if j == i:
+                assert S[0] > 0, i
+                n, e = rii
+                v, ulp = F(rii), Fraction(2) ** e
+                below = ulp / 4 if n == 1 << (P - 1) else ulp / 2
+                lo2, hi2, s = (v - below) ** 2, (v + ulp / 2) ** 2, F(S)
+                assert lo2 <= s <= hi2, (i, "sqrt")
+                if s in (lo2, hi2):
+                    assert n % 2 == 0, (i, "sqrt tie")
+            else:
+                assert R[i][j - i] == round_fraction(F(S) / F(rii), P), (i, j)
+
+
+@pytest.mark.parametrize("beta,N,P", [((1, 1), 24, 256), ((7, 4), 40, 384), ((3, 4), 40, 384),
+                                      ((3, 2), 24, 512), ((2, 1), 17, 320)])
+def test_every_rounding_audited(beta, N, P):
+    """The oracle's R, entry by entry, is the once-rounded value its
+    definition gives (the same R the device parity tests compare bit for bit)."""
+    m = inputs.moments(N, beta, P)
+    _audit(m, H.cholesky(m, N, P), P)
+
+
+def test_audit_catches_a_one_ulp_error():
+    N, P = 12, 128
+    m = inputs.moments(N, (7, 4), P)
+    R = H.cholesky(m, N, P)
+    n, e = R[5][3]
+    R[5][3] = (n + 1, e)  # one ulp off in row 5
+    with pytest.raises(AssertionError):
+        _audit(m, R, P)
+
+
 def test_beta74_N4_worked_example():
     P = 128
     m = inputs.moments(4, (7, 4), P)
