@@ -121,6 +121,15 @@ def oracle_sample(pool, cores, N, P, row0, last, setup):
     return macs, max(busy.values())
 
 
+def oracle_single_thread(N, P, row0, setup, ncols=64):
+    """The oracle on one core: row row0 for its first `ncols` columns, in this
+    process.  Returns (MACs, seconds)."""
+    m, col = setup
+    js = list(range(row0, min(N, row0 + ncols)))
+    _, macs, sec = _oracle_chunk(([row0], m, {row0: col[row0][:row0]}, {j: col[j] for j in js}, P))
+    return macs, sec
+
+
 def sample_rows(N):
     row0 = N // 2
     return row0, min(N, row0 + ORACLE_ROWS)
@@ -199,6 +208,7 @@ def run_reference(args):
         tot_m += m
         tot_t += t
     pool.shutdown()
+    m1, t1 = oracle_single_thread(N, P, row0, setup)
     v = tot_m / tot_t
     sample = (f"{last - row0} panel steps (rows {row0}..{last - 1}) of the N={N}, P={P}, beta=1 factorisation, "
               f"all columns ({tot_m // args.steps} MACs per step; time in the oracle, inputs shipped untimed)")
@@ -209,7 +219,9 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": f"Hankel moment matrix N={N}, beta=1 (m_k = k!), P={P} bits; oracle sample", "N": N,
                    "P": P, "beta": "1"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "single_thread": {"value": m1 / t1, "unit": UNIT,
+                                           "sample": f"row {row0}, first 64 columns ({m1} MACs, one process)"}},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -238,10 +250,13 @@ def main():
         setup = oracle_sample_setup(N, P, row0, last)
         m_, t_ = oracle_sample(pool, cores, N, P, row0, last, setup)
         pool.shutdown()
+        m1, t1 = oracle_single_thread(N, P, row0, setup)
         cpu = {"value": m_ / t_, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{last - row0} panel steps (rows {row0}..{last - 1}) of the N={N}, P={P}, beta=1 "
                          f"factorisation, all columns ({m_} MACs, {t_:.1f} s in the oracle, inputs shipped "
-                         f"untimed)"}
+                         f"untimed)",
+               "single_thread": {"value": m1 / t1, "unit": UNIT,
+                                 "sample": f"row {row0}, first 64 columns ({m1} MACs, one process)"}}
 
     import numpy as np
     import torch
