@@ -52,3 +52,34 @@ def test_pack_roundtrip():
     from paper_0902_0852_gb300 import hk, inputs
     vals = inputs.moments(6, (7, 4), 96) + [(0, 0), (-(1 << 95) - 5, -7)]
     assert hk.unpack(*hk.pack(vals, 96)) == vals
+
+
+def test_every_entry_point_rejects_a_null_context_or_bad_argument(lib):
+    """Status codes, never an abort: with no context (or an out-of-range
+    operation) every entry point returns HK_ERR_ARG without touching a GPU."""
+    ARG = 1
+    calls = [
+        lambda: lib.hk_create(None, 0, None),
+        lambda: lib.hk_set_workspace(None, None, 0),
+        lambda: lib.hk_load_moments(None, 4, 1, 1, 64, None),
+        lambda: lib.hk_load_moments_flat(None, 4, 1, 1, 64, None, None, None, 0),
+        lambda: lib.hk_factor(None, None),
+        lambda: lib.hk_get_R(None, None),
+        lambda: lib.hk_get_R_flat(None, None, None, None),
+        lambda: lib.hk_smallest_eig(None, 1, None, None),
+        lambda: lib.hk_get_history_flat(None, 1, None, None, None),
+        lambda: lib.hk_get_timings(None, None, 1),
+        lambda: lib.hk_get_stats(None, None, 1),
+        lambda: lib.hk_set_update_path(None, 0),
+        lambda: lib.hk_set_option(None, 0, 0),
+        lambda: lib.hk_batch_solve(None, 1, None, None, None, None, None, 0, 1, None, None, None),
+        lambda: lib.hk_set_predictor(None, None, None),
+        lambda: lib.hk_predict(None, 1, None, None, None),
+        lambda: lib.hk_selftest_mp(9, 1, None, 0, 0, None, 0, 0, None, None),
+        lambda: lib.hk_mp_op_noalloc(9, 1, None, 0, 0, None, 0, 0, None, None, None),
+        lambda: lib.hk_probe_int_peaks(0, None, 0),
+        lambda: lib.hk_mlp_forward(None, None, 0, None, None),
+        lambda: lib.hk_update_plan(0, -1, None, None, None, None, None, 0, None),
+    ]
+    for k, call in enumerate(calls):
+        assert call() == ARG, k
