@@ -12,8 +12,9 @@
 // Karatsuba on the whole dot product: with a = a0 + a1 B,
 //   sum a_i a_j = C0 + B (Cs - C0 - C1) + B^2 C1,
 //   C0 = sum a0_i a0_j, C1 = sum a1_i a1_j, Cs = sum (a0+a1)_i (a0+a1)_j,
-// so one launch runs a list of smaller contractions ("sub-problems", up to
-// nine for two levels), each added to the column sums at (offset, sign) terms.
+// so one launch runs a list of smaller contractions ("sub-problems", 3^levels
+// for up to three levels), each added to the column sums at its (offset, sign)
+// terms (up to 2^levels of them).
 // The identity is exact, so results do not depend on the expansion depth.
 //
 // Layout of the work: the wx x wy grid of limb products (p, q) of one
