@@ -20,6 +20,12 @@ large ill-conditioned Hankel matrices"):
   quotient of M^-1 (section "M is extremely ill-conditioned" uses the Rayleigh
   quotient to bound the spectrum), giving ``lambda_min``.
 
+* the paper's own method (``secant.py``): the smallest root of
+  ``P(x) = det(M - xI)`` by the Secant recurrence (section "The Secant
+  Algorithm"), P(x) from an LDL^T of ``M - xI`` (section "The LDL^T
+  Determinant Algorithm"), and the root proved by the sign of the determinant
+  just below and above it (section "Interval Verification").
+
 All arithmetic is exact Python-integer arithmetic; the only rounding is the
 explicit ``rne`` of an exact value.  Every function cites the passage it follows.
 """
