@@ -319,26 +319,14 @@ static cudaError_t set_smem(const void *fn, size_t bytes) {
   return bytes > 48 * 1024 ? allow_dynamic_smem(fn) : cudaSuccess;
 }
 
-// threads per CTA (templated for tuning; fewer threads measured slower)
-static int diag_threads(int L) {
-  (void)L;
-  return NT_DIAG;
-}
-
-template <int NT>
-static cudaError_t launch_diag_t(const PanelParams &p, int i, cudaStream_t s) {
-  const size_t smem = panel_smem_diag(p.L, p.C);
-  cudaError_t e = set_smem((const void *)k_diag<NT>, smem);
-  if (e != cudaSuccess) return e;
-  k_diag<NT><<<1, NT, smem, s>>>(p, i);
-  return cudaGetLastError();
-}
-
+// one CTA of NT_DIAG threads per row (256 and 128 threads measured slower:
+// the work of each phase is parallel over result columns)
 cudaError_t launch_diag(const PanelParams &p, int i, cudaStream_t s) {
-  switch (diag_threads(p.L)) {
-    case 256: return launch_diag_t<256>(p, i, s);
-    default: return launch_diag_t<NT_DIAG>(p, i, s);
-  }
+  const size_t smem = panel_smem_diag(p.L, p.C);
+  cudaError_t e = set_smem((const void *)k_diag<NT_DIAG>, smem);
+  if (e != cudaSuccess) return e;
+  k_diag<NT_DIAG><<<1, NT_DIAG, smem, s>>>(p, i);
+  return cudaGetLastError();
 }
 
 template <int NT>

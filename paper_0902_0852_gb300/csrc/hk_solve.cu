@@ -525,50 +525,28 @@ cudaError_t set_smem(const void *fn, size_t bytes) {
 
 }  // namespace
 
-// threads per CTA of the single-CTA solve kernels (templated for tuning; fewer
-// threads measured slower at every precision: the work of an entry is
-// parallel over its result columns)
-int solve_threads(int L) {
-  (void)L;
-  return NT_SOLVE;
-}
-
-template <int NT>
-cudaError_t launch_solve_entry_t(const SolveParams &p, int i, cudaStream_t s) {
-  const size_t smem = ssmem_size(p.L, p.C, false);
-  cudaError_t e = set_smem((const void *)k_solve_entry<NT>, smem);
-  if (e != cudaSuccess) return e;
-  k_solve_entry<NT><<<1, NT, smem, s>>>(p, i);
-  return cudaGetLastError();
-}
-
+// the single-CTA solve kernels run NT_SOLVE threads (fewer threads measured
+// slower at every precision: the work of an entry is parallel over its result
+// columns)
 cudaError_t launch_solve_entry(const SolveParams &p, int i, cudaStream_t s) {
-  switch (solve_threads(p.L)) {
-    case 256: return launch_solve_entry_t<256>(p, i, s);
-    default: return launch_solve_entry_t<NT_SOLVE>(p, i, s);
-  }
+  const size_t smem = ssmem_size(p.L, p.C, false);
+  cudaError_t e = set_smem((const void *)k_solve_entry<NT_SOLVE>, smem);
+  if (e != cudaSuccess) return e;
+  k_solve_entry<NT_SOLVE><<<1, NT_SOLVE, smem, s>>>(p, i);
+  return cudaGetLastError();
 }
 
 size_t solve_block_smem(int L, int C, int W, int Wv, int nb) {
   return block_smem_size(L, C, W, Wv, nb, nullptr, nullptr);
 }
 
-template <int NT>
-cudaError_t launch_solve_block_t(const SolveParams &p, const uint32_t *A, const int32_t *Asign, int B0, int B1,
-                                 cudaStream_t s) {
-  const size_t smem = block_smem_size(p.L, p.C, p.W, p.Wv, B1 - B0, nullptr, nullptr);
-  cudaError_t e = set_smem((const void *)k_solve_block<NT>, smem);
-  if (e != cudaSuccess) return e;
-  k_solve_block<NT><<<1, NT, smem, s>>>(p, A, Asign, B0, B1);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_solve_block(const SolveParams &p, const uint32_t *A, const int32_t *Asign, int B0, int B1,
                                cudaStream_t s) {
-  switch (solve_threads(p.L)) {
-    case 256: return launch_solve_block_t<256>(p, A, Asign, B0, B1, s);
-    default: return launch_solve_block_t<NT_SOLVE>(p, A, Asign, B0, B1, s);
-  }
+  const size_t smem = block_smem_size(p.L, p.C, p.W, p.Wv, B1 - B0, nullptr, nullptr);
+  cudaError_t e = set_smem((const void *)k_solve_block<NT_SOLVE>, smem);
+  if (e != cudaSuccess) return e;
+  k_solve_block<NT_SOLVE><<<1, NT_SOLVE, smem, s>>>(p, A, Asign, B0, B1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_vec_exprange(int n, MpArr v, int L, const long long *off, int scaled, long long *out2,
