@@ -464,3 +464,22 @@ def test_planted_truncating_sqrt_is_caught(monkeypatch):
     monkeypatch.setattr(H, "mp_sqrt", trunc_sqrt)
     with pytest.raises(AssertionError):
         test_sqrt_correctly_rounded()
+
+
+def test_golden_beta1_digest_is_the_closed_form():
+    """The stored digest of the N = 256, P = 8192, beta = 1 factor (written by
+    tests/golden/make_golden.py from the oracle) equals the digest of the
+    closed form R_ki = i! C(i, k), rounded to P bits -- a pin of the stored
+    value that does not run the oracle."""
+    import importlib.util
+    import json
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "golden", "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    with open(os.path.join(here, "golden", "config2_beta1.json")) as f:
+        g = json.load(f)
+    N, P = g["N"], g["P"]
+    R = [[H.rne(factorial(j) * comb(j, t), 0, P) for j in range(t, N)] for t in range(N)]
+    assert mg.digest_R(R, P) == g["R_sha256"]
