@@ -263,3 +263,21 @@ def test_some_widening_resumed():
     if not RESUMES:
         pytest.skip("widening cases did not run")
     assert max(RESUMES) >= 1, RESUMES
+
+
+def test_sampled_rows_beyond_the_configs(hk):
+    """N = 512, beta = 7/4, P = 8192 (a shape no stored value covers): sampled
+    rows of the device factor -- the first, both sides of panel-block edges,
+    the middle and the last -- equal the oracle's row routine applied to the
+    device's own rows above them (tests/rowcheck.py), bit for bit."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from rowcheck import check_rows
+    N, beta, P = 512, (7, 4), 8192
+    m = inputs.moments(N, beta, P)
+    with hk.Hankel(0) as h:
+        h.load(N, beta, P, m)
+        h.factor()
+        R = h.R()
+    assert check_rows(m, R, P, [0, 1, 15, 16, 17, 255, 256, 300, 511], max_cols=64) == []
