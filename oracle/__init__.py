@@ -37,6 +37,7 @@ from .hankel import (  # noqa: F401
     exact_dot,
     cholesky,
     cholesky_row,
+    cholesky_factorial,
     forward_solve,
     back_solve,
     rayleigh_lambda,

@@ -197,6 +197,39 @@ def cholesky(moments, N, P, rows=None, workers=1):
     return R
 
 
+def cholesky_factorial(N, P):
+    """R of the beta = 1 matrix (m_k = k!, the paper's first N = 4 example)
+    when P is wide enough for every step of ``cholesky`` to be exact.
+
+    Vandermonde's identity sum_t C(i,t) C(j,t) = C(i+j, i) gives
+    M = R^T R with the integer factor R_ti = i! C(i, t) (t <= i).  Then
+    A_ij = R_ii R_ij = i! j! C(j, i) <= (i+j)!, R_ii = i! and R_ij = j! C(j, i):
+    integers below 2^P whenever (2N-2)! < 2^P, so the square root, the
+    quotient and every rounding of reading 1 are exact and ``cholesky``
+    returns exactly these values.  This is that result written out (it needs
+    no O(N^3) arithmetic); P too small for exactness raises ValueError.
+    Same layout as ``cholesky``: ``R[t][j - t] = R_tj``.
+    """
+    f = 1
+    for k in range(2, 2 * N - 1):
+        f *= k
+    if N > 0 and f.bit_length() > P:
+        raise ValueError(f"(2N-2)! has {f.bit_length()} bits > P = {P}: not exact")
+    fact = [1] * max(N, 1)
+    for k in range(1, N):
+        fact[k] = fact[k - 1] * k
+    R = []
+    for t in range(N):
+        row = []
+        c = 1  # C(j, t) at j = t
+        for j in range(t, N):
+            if j > t:
+                c = c * j // (j - t)
+            row.append(rne(fact[j] * c, 0, P))
+        R.append(row)
+    return R
+
+
 # ---------------------------------------------------------------------------
 # Inverse iteration (reading 4)
 # ---------------------------------------------------------------------------

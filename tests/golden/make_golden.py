@@ -6,7 +6,7 @@ layout (sign int32, exp int64, L little-endian limbs per entry, entries in
 row-major packed upper-triangle order) and the inverse-iteration history
 lambda_1..lambda_T as (mantissa, exponent) pairs.
 
-Usage: python tests/golden/make_golden.py [workers]
+Usage: python tests/golden/make_golden.py [workers] [case names ...]
 """
 import hashlib
 import json
@@ -20,6 +20,9 @@ CASES = [
     # name, N, beta, P, T
     ("config2_beta1", 256, (1, 1), 8192, 10),
     ("config2_beta7_4", 256, (7, 4), 8192, 10),
+    # the paper-scale factorial matrix: every step of the factorisation is exact
+    # at this P, so the oracle's factor is its closed form (cholesky_factorial)
+    ("paper_scale_beta1", 1000, (1, 1), 24576, 3),
 ]
 
 
@@ -39,9 +42,15 @@ def main():
     import oracle
     from paper_0902_0852_gb300 import inputs
     workers = int(sys.argv[1]) if len(sys.argv) > 1 else (os.cpu_count() or 1)
+    only = set(sys.argv[2:])
     for name, N, beta, P, T in CASES:
-        m = inputs.moments(N, beta, P)
-        R = oracle.cholesky(m, N, P, workers=workers)
+        if only and name not in only:
+            continue
+        if beta == (1, 1) and N >= 1000:
+            R = oracle.cholesky_factorial(N, P)
+        else:
+            m = inputs.moments(N, beta, P)
+            R = oracle.cholesky(m, N, P, workers=workers)
         lam, hist, _ = oracle.inverse_iteration(R, P, T)
         out = {"N": N, "beta": list(beta), "P": P, "T": T, "R_sha256": digest_R(R, P),
                "history": [[str(n), e] for n, e in hist]}
