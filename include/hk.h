@@ -129,10 +129,27 @@ int hk_set_update_path(hk_ctx *ctx, int path);
  *   HK_OPT_PANEL_ROWS       rows per panel block, 1..256 (default 16)
  *   HK_OPT_MAX_ITERS        step cap of hk_smallest_eig with iters = 0,
  *                           1..100000 (default 200); keeps the factorisation
+ *   HK_OPT_WAIT_NS          limit in nanoseconds of every bounded device wait
+ *                           of this context's kernels (a pipeline stage that
+ *                           never fills, a copy that never lands), 1000 ..
+ *                           6e10 (default 2e9); a wait that runs out makes its
+ *                           kernel record the timeout and return, and the call
+ *                           returns HK_ERR_TIMEOUT; keeps the factorisation
  * None of the first five changes any result: every sum is exact. */
 enum { HK_OPT_UPDATE_PATH = 0, HK_OPT_KARATSUBA = 1, HK_OPT_GRAPH = 2, HK_OPT_AUTOTUNE = 3, HK_OPT_PANEL_ROWS = 4,
-       HK_OPT_MAX_ITERS = 5 };
+       HK_OPT_MAX_ITERS = 5, HK_OPT_WAIT_NS = 6 };
 int hk_set_option(hk_ctx *ctx, int option, long long value);
+
+/* Failure-detection self-test (no counterpart in the paper): on the context's
+ * stream, one block arms a shared-memory barrier for a transfer that is never
+ * issued and waits on it with the same bounded wait the update kernels use,
+ * limited by HK_OPT_WAIT_NS.  The wait runs out, the kernel records the
+ * timeout in the context's device status word and returns -- no hang, no
+ * fault -- and the call returns HK_ERR_TIMEOUT (HK_OK would mean the wait
+ * was not bounded as designed).  The status word is cleared afterwards, so
+ * the context and any factorisation it holds stay usable.  Requires loaded
+ * moments (HK_ERR_STATE otherwise). */
+int hk_selftest_wait(hk_ctx *ctx);
 
 /* Solve `count` independent instances (moments[k] holds the 2N[k]-1 host
  * moments of instance k at precision P[k]); beta is recorded for reporting.
@@ -143,7 +160,10 @@ int hk_set_option(hk_ctx *ctx, int option, long long value);
  * `iters` steps of inverse iteration (0 = until converged), iters_out[k] (may
  * be NULL) the steps taken, negated when iters = 0 and the step cap
  * (HK_OPT_MAX_ITERS) ended the iteration before the convergence test was met.
- * Returns HK_OK unless a worker could not start. */
+ * Every status_out[k] is written: an instance no worker reached (no worker
+ * could start) keeps HK_ERR_CUDA.  Returns HK_OK when at least one worker
+ * started (each instance then carries its own status), HK_ERR_CUDA when none
+ * could. */
 int hk_batch_solve(hk_ctx *ctx, int count, const int *N, const int *beta_num, const int *beta_den,
                    const int *P, const hk_mp *const *moments, int iters, int nthreads,
                    hk_mp *lambda_out, int *status_out, int *iters_out);
@@ -191,7 +211,10 @@ int hk_get_stats(hk_ctx *ctx, int64_t *out, int n);
  * accumulation form of the update kernel (mad.lo.cc/madc.hi.cc/addc), out[3]
  * its clock; out[4] u8 multiply-adds per clock per SM of mma.sync m16n8k32
  * (the warp-level INT8 tensor instruction), out[5] its clock.  n >= 6.
- * There is no counterpart in the paper: it measures the roofline denominator. */
+ * There is no counterpart in the paper: it measures the roofline denominator.
+ * Makes `device` current for the calling thread; its work runs on a private
+ * non-blocking stream (events and copies ordered on it), so it neither waits
+ * for nor blocks other streams, and several host threads may call it. */
 int hk_probe_int_peaks(int device, double *out, int n);
 
 /* ----- self-test hooks of the device multiprecision library ----------------
@@ -202,7 +225,9 @@ int hk_probe_int_peaks(int device, double *out, int n);
  *   op 2: out = RNE_P(sqrt(x * 2^e)) mantissa, *eo exponent (x: L limbs)
  *   op 3: out = RNE_P((x 2^e) / (y 2^f)) mantissa, *eo exponent
  *   op 4: out = RNE_P(|x| 2^e) of an nx-limb integer, *eo exponent
- * `out` has room for the stated limbs. */
+ * `out` has room for the stated limbs.  Runs on the calling thread's current
+ * device, on a private non-blocking stream (stream-ordered copies, then a
+ * synchronisation of that stream only); safe from several host threads. */
 int hk_selftest_mp(int op, int L, const uint32_t *x, int nx, int64_t ex,
                    const uint32_t *y, int ny, int64_t ey, uint32_t *out, int64_t *eo);
 
@@ -220,7 +245,8 @@ int hk_selftest_mp(int op, int L, const uint32_t *x, int nx, int64_t ex,
  *
  * No memory is allocated: the work area is one fixed device array of about
  * 1.3 MB inside the library (every GPU that loads the library holds it until
- * the process exits), so sizes are limited to nx + ny + L <= 4096 limbs;
+ * the process exits), so sizes are limited to nx + ny + L <= 4096 limbs, and
+ * ops 1-4 to P = 32 L <= 32768 bits (the range their error bounds cover);
  * larger requests return HK_ERR_ARG.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress, with that device current);
  * make that first call before any stream capture.  All calls share the one

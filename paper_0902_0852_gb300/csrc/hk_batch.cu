@@ -26,6 +26,12 @@ extern "C" int hk_batch_solve_impl(hk_ctx *parent, int device, const long long *
     if (N[k] < 1 || P[k] < 32 || P[k] % 32 || !moments[k] || !lambda_out[k].limbs) return HK_ERR_ARG;
   if (count == 0) return HK_OK;
   (void)parent;
+  // every instance reports its own outcome; one that no worker reaches keeps
+  // this code
+  for (int k = 0; k < count; k++) {
+    status_out[k] = HK_ERR_CUDA;
+    if (iters_out) iters_out[k] = 0;
+  }
   std::vector<int> order(count);
   for (int k = 0; k < count; k++) order[k] = k;
   std::sort(order.begin(), order.end(), [&](int a, int b) {
@@ -35,23 +41,17 @@ extern "C" int hk_batch_solve_impl(hk_ctx *parent, int device, const long long *
   });
   const int nw = std::max(1, std::min(nthreads, count));
   std::atomic<int> next(0);
-  std::atomic<int> fatal(HK_OK);
+  std::atomic<int> started(0);
   auto worker = [&]() {
-    if (cudaSetDevice(device) != cudaSuccess) {
-      fatal = HK_ERR_CUDA;
-      return;
-    }
+    if (cudaSetDevice(device) != cudaSuccess) return;
     cudaStream_t s = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-      fatal = HK_ERR_CUDA;
-      return;
-    }
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
     hk_ctx *w = nullptr;
     if (hk_create(&w, device, s) != HK_OK) {
       cudaStreamDestroy(s);
-      fatal = HK_ERR_CUDA;
       return;
     }
+    started.fetch_add(1);
     for (int o = 0; o < 6; o++) hk_set_option(w, o, opts[o]);
     for (;;) {
       const int q = next.fetch_add(1);
@@ -75,5 +75,7 @@ extern "C" int hk_batch_solve_impl(hk_ctx *parent, int device, const long long *
   std::vector<std::thread> pool;
   for (int t = 0; t < nw; t++) pool.emplace_back(worker);
   for (auto &th : pool) th.join();
-  return fatal.load();
+  // HK_ERR_CUDA only when no worker could start (then no instance ran); a
+  // worker that failed to start leaves its share to the others
+  return started.load() > 0 ? HK_OK : HK_ERR_CUDA;
 }

@@ -98,23 +98,32 @@ int run_probe(Probe fn, int iters, double ops_per_thread_iter, double *per_clk_s
   const int blocks = nsm * 8, threads = 256;
   uint32_t *dout = nullptr;
   Stamp *dst = nullptr;
-  if (cudaMalloc(&dout, (size_t)blocks * threads * 4) != cudaSuccess) return HK_ERR_OOM;
-  if (cudaMalloc(&dst, (size_t)blocks * sizeof(Stamp)) != cudaSuccess) {
-    cudaFree(dout);
+  // a private non-blocking stream: launches, events and the stamp copy are
+  // ordered on it (no legacy-stream synchronous copies)
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return HK_ERR_CUDA;
+  if (cudaMalloc(&dout, (size_t)blocks * threads * 4) != cudaSuccess) {
+    cudaStreamDestroy(s);
     return HK_ERR_OOM;
   }
-  fn<<<blocks, threads>>>(dout, 4, 1u, dst);
+  if (cudaMalloc(&dst, (size_t)blocks * sizeof(Stamp)) != cudaSuccess) {
+    cudaFree(dout);
+    cudaStreamDestroy(s);
+    return HK_ERR_OOM;
+  }
+  fn<<<blocks, threads, 0, s>>>(dout, 4, 1u, dst);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  cudaEventRecord(e0);
-  fn<<<blocks, threads>>>(dout, iters, 12345u, dst);
-  cudaEventRecord(e1);
+  cudaEventRecord(e0, s);
+  fn<<<blocks, threads, 0, s>>>(dout, iters, 12345u, dst);
+  cudaEventRecord(e1, s);
   cudaError_t e = cudaEventSynchronize(e1);
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
   Stamp *h = new Stamp[blocks];
-  if (e == cudaSuccess) e = cudaMemcpy(h, dst, blocks * sizeof(Stamp), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, dst, blocks * sizeof(Stamp), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   double cyc = 0, ns = 0;
   for (int b = 0; b < blocks; b++) {
     cyc += (double)(h[b].c1 - h[b].c0);
@@ -125,6 +134,7 @@ int run_probe(Probe fn, int iters, double ops_per_thread_iter, double *per_clk_s
   cudaEventDestroy(e1);
   cudaFree(dout);
   cudaFree(dst);
+  cudaStreamDestroy(s);
   if (e != cudaSuccess || ms <= 0 || ns <= 0) return HK_ERR_CUDA;
   *mhz = cyc / ns * 1e3;
   const double rate = ops_per_thread_iter * iters * (double)blocks * threads / (ms * 1e-3);

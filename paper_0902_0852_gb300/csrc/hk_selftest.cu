@@ -68,24 +68,28 @@ int selftest_mp(int op, int L, const uint32_t *x, int nx, int64_t ex, const uint
   auto ck = [&](cudaError_t e) {
     if (e != cudaSuccess && rc == 0) rc = 3;
   };
+  // everything on a private non-blocking stream, ordered copies in and out
+  // (no legacy-stream or pageable synchronous copies)
+  cudaStream_t s = nullptr;
+  ck(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   ck(cudaMalloc(&dx, 4 * (size_t)(nx + 1)));
   ck(cudaMalloc(&dy, 4 * (size_t)(ny + 1)));
   ck(cudaMalloc(&dout, 4 * (size_t)(cap)));
   ck(cudaMalloc(&scr, 4 * (size_t)cap * 14));
   ck(cudaMalloc(&dcs, 8 * (size_t)cap));
   ck(cudaMalloc(&deo, 16));
+  long long h[2] = {0, 0};
   if (rc == 0) {
-    ck(cudaMemcpy(dx, x, 4 * (size_t)nx, cudaMemcpyHostToDevice));
-    if (ny) ck(cudaMemcpy(dy, y, 4 * (size_t)ny, cudaMemcpyHostToDevice));
-    ck(cudaMemset(deo, 0, 16));
-    ck(cudaMemset(dout, 0, 4 * (size_t)cap));
-    ck(cudaMemset(scr, 0, 4 * (size_t)cap * 14));
-    k_selftest<<<1, NT_ST>>>(op, L, dx, nx, ex, dy, ny, ey, dout, deo, scr, dcs, cap);
+    ck(cudaMemcpyAsync(dx, x, 4 * (size_t)nx, cudaMemcpyHostToDevice, s));
+    if (ny) ck(cudaMemcpyAsync(dy, y, 4 * (size_t)ny, cudaMemcpyHostToDevice, s));
+    ck(cudaMemsetAsync(deo, 0, 16, s));
+    ck(cudaMemsetAsync(dout, 0, 4 * (size_t)cap, s));
+    ck(cudaMemsetAsync(scr, 0, 4 * (size_t)cap * 14, s));
+    if (rc == 0) k_selftest<<<1, NT_ST, 0, s>>>(op, L, dx, nx, ex, dy, ny, ey, dout, deo, scr, dcs, cap);
     ck(cudaGetLastError());
-    ck(cudaDeviceSynchronize());
-    ck(cudaMemcpy(out, dout, 4 * (size_t)nout, cudaMemcpyDeviceToHost));
-    long long h[2] = {0, 0};
-    ck(cudaMemcpy(h, deo, 16, cudaMemcpyDeviceToHost));
+    ck(cudaMemcpyAsync(out, dout, 4 * (size_t)nout, cudaMemcpyDeviceToHost, s));
+    ck(cudaMemcpyAsync(h, deo, 16, cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
     eo[0] = h[0];
     eo[1] = h[1];
   }
@@ -95,6 +99,7 @@ int selftest_mp(int op, int L, const uint32_t *x, int nx, int64_t ex, const uint
   cudaFree(scr);
   cudaFree(dcs);
   cudaFree(deo);
+  if (s) cudaStreamDestroy(s);
   return rc;
 }
 
@@ -143,7 +148,11 @@ extern "C" int hk_mp_op_noalloc(int op, int L, const uint32_t *x, int nx, int64_
     return HK_ERR_ARG;
   if ((op == 1 || op == 2) && nx != L) return HK_ERR_ARG;
   if (op == 3 && (nx != L || ny != L)) return HK_ERR_ARG;
-  if (nx + ny + L > NOALLOC_MAX_LIMBS) return HK_ERR_ARG;
+  // each size against the limit before any sum (no int overflow); the rounded
+  // operations are argued for P = 32 L <= 32768 bits
+  if (L > NOALLOC_MAX_LIMBS || nx > NOALLOC_MAX_LIMBS || ny > NOALLOC_MAX_LIMBS) return HK_ERR_ARG;
+  if ((long long)nx + ny + L > NOALLOC_MAX_LIMBS) return HK_ERR_ARG;
+  if (op >= 1 && 32LL * L > 32768) return HK_ERR_ARG;
   unsigned char *area = nullptr;
   if (noalloc_area(&area) != cudaSuccess) return HK_ERR_CUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

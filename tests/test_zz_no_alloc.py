@@ -42,8 +42,10 @@ def test_noalloc_matches_allocating_entry_point():
         nout = {0: nx + ny + 2, 1: L + 2}.get(op, L)
         xd = dev(_limbs(x, nx))
         yd = dev(_limbs(y, ny)) if y is not None else None
-        out = torch.zeros(nout, dtype=torch.int32, device="cuda")
-        eo = torch.zeros(2, dtype=torch.int64, device="cuda")
+        # dirty output buffers (all ones): the result must not depend on
+        # what the caller's memory held before the call
+        out = torch.full((nout,), -1, dtype=torch.int32, device="cuda")
+        eo = torch.full((2,), -1, dtype=torch.int64, device="cuda")
         hk.hk_mp_op_noalloc(op, L, xd, ex, yd, ey, out, eo, stream)
         torch.cuda.synchronize()
         val = int.from_bytes(out.cpu().numpy().view(np.uint32).tobytes(), "little")
@@ -64,3 +66,9 @@ def test_noalloc_rejects_oversized_requests():
     with pytest.raises(hk.HKError) as ei:
         hk.hk_mp_op_noalloc(0, 1, x, 0, y, 0, out, eo)
     assert ei.value.code == hk.HK_ERR_ARG
+    # rounded operations are limited to P = 32 L <= 32768 bits: L = 1025 is
+    # refused although nx + ny + L stays within the work area
+    for op, L, nx, ny in [(1, 1025, 1025, 0), (2, 1025, 1025, 0), (3, 1025, 1025, 1025), (4, 1025, 8, 0)]:
+        with pytest.raises(hk.HKError) as ei:
+            hk.hk_mp_op_noalloc(op, L, x[:nx], 0, None if ny == 0 else x[:ny], 0, out, eo)
+        assert ei.value.code == hk.HK_ERR_ARG, (op, L)
