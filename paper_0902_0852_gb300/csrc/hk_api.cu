@@ -96,6 +96,7 @@ struct hk_ctx {
   bool use_graph = false;    // capture each factorisation in a CUDA graph
   cudaStream_t cap_stream = nullptr;  // capture stream when `stream` is a default stream
   int max_iters = 200;       // step cap of hk_smallest_eig(iters = 0)
+  long long wait_ns = 0;     // limit of each bounded device wait (0: the kernels' default, 2 s)
   float *pred_params = nullptr;  // predictor network on the device (hk_set_predictor)
   double pred_scales[10] = {0};
   float *pred_buf = nullptr;     // inputs and outputs of hk_predict
@@ -303,6 +304,7 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
       ok = cudaMemcpyAsync(units, h.data(), sizeof(Unit) * n, cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
       UpdParams up;
       std::memset(&up, 0, sizeof(up));
+      up.wait_ns = c->wait_ns;
       const int maxlen = operand_windows(sub, nsub, h.data(), n, ((KAR_GAP + 3) / 4) * 4, stride, up.xlo, up.xlen);
       up.nxb = maxlen > 0 ? (n + UNT - 1) / UNT : 0;
       up.mode = M_FACTOR;
@@ -633,6 +635,7 @@ int factor_enqueue(hk_ctx *c, const Sched &sc, int r_start) {
 
   UpdParams up;
   std::memset(&up, 0, sizeof(up));
+  up.wait_ns = c->wait_ns;
   up.mode = M_FACTOR;
   up.N = N;
   up.A = levels > 0 ? c->Aexp : c->A;
@@ -853,6 +856,7 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
       }
       UpdParams up;
       std::memset(&up, 0, sizeof(up));
+      up.wait_ns = c->wait_ns;
       up.mode = back ? M_GEMV_BACK : M_GEMV_FWD;
       up.N = N;
       up.A = lv > 0 ? c->Aexp : c->A;
@@ -978,6 +982,7 @@ int rayleigh(hk_ctx *c, int slot) {
   CK(cudaMemsetAsync(c->colsum_s, 0, sizeof(long long) * 2 * Cd, c->stream));
   UpdParams up;
   std::memset(&up, 0, sizeof(up));
+  up.wait_ns = c->wait_ns;
   up.mode = M_DOT;
   up.N = N;
   up.Vx = c->vecA;
@@ -1313,6 +1318,20 @@ int hk_factor(hk_ctx *c, int *bad_row) {
   return result;
 }
 
+int hk_selftest_wait(hk_ctx *c) {
+  if (!c) return HK_ERR_ARG;
+  if (!c->loaded) return HK_ERR_STATE;
+  CK(reset_status(c));
+  CK(launch_wait_selftest(c->st, c->wait_ns, c->stream));
+  const DevStatus st = read_status(c);
+  CK(cudaGetLastError());
+  // the wait touched nothing but the status word: clear it so that the
+  // context (and a factorisation it holds) stays usable
+  CK(reset_status(c));
+  CK(cudaStreamSynchronize(c->stream));
+  return (st.timeout > 0 && st.code == ST_TIMEOUT) ? HK_ERR_TIMEOUT : HK_OK;
+}
+
 int hk_set_option(hk_ctx *c, int option, long long value) {
   if (!c) return HK_ERR_ARG;
   switch (option) {
@@ -1336,6 +1355,10 @@ int hk_set_option(hk_ctx *c, int option, long long value) {
     case 5:  // step cap of the converging inverse iteration (R stays valid)
       if (value < 1 || value > 100000) return HK_ERR_ARG;
       c->max_iters = (int)value;
+      return HK_OK;
+    case 6:  // limit of each bounded device wait, ns (R stays valid)
+      if (value < 1000 || value > 60000000000LL) return HK_ERR_ARG;
+      c->wait_ns = value;
       return HK_OK;
     default:
       return HK_ERR_ARG;

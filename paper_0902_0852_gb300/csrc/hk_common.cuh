@@ -65,6 +65,13 @@ struct MpArr {
   uint32_t *limbs;
 };
 
+// A bounded wait ran out: count it and stop the sequence (later kernels test
+// the code on entry and return).
+HK_DEV void raise_timeout(DevStatus *st) {
+  atomicAdd(&st->timeout, 1);
+  atomicCAS(&st->code, ST_OK, ST_TIMEOUT);
+}
+
 HK_DEV void raise_range(DevStatus *st, long long need) {
   atomicAdd(&st->range_fail, 1);
   atomicMax(&st->need_bits, need);

@@ -19,7 +19,8 @@ constexpr int UC = 9;          // default stripe width (result columns per threa
 constexpr int UC_MAX = 13;
 constexpr int UPC = 36;        // default p-steps per unit (a multiple of the stripe width)
 constexpr int UNT = 256;       // compute threads per CTA
-constexpr int USTAGES = 4;     // shared-memory pipeline depth
+constexpr int USTAGES = 4;     // default shared-memory pipeline depth
+constexpr int USTAGES_MAX = 8; // deepest ring a launch may use
 constexpr int MAX_KAR = 3;     // Karatsuba levels of the expansion
 constexpr int MAX_SUB = 27;    // sub-contractions per launch (3^levels)
 constexpr int MAX_TERMS = 8;   // result positions a sub-contraction is added to (2^levels)
@@ -85,6 +86,8 @@ struct UpdParams {
   int nout;                // number of outputs
   int t0, t1;              // contraction range [t0, t1)
   int tchunk;              // t per CTA (z dimension)
+  int nst;                 // pipeline stages of the launch (2..USTAGES_MAX; set by the launcher)
+  long long wait_ns;       // limit of each bounded device wait (0: the default, 2 s)
   long long *colsum;       // [outputs][C] signed 64-bit column sums (accumulated)
   int C;
   long long a_len, vx_len, vy_len, colsum_len;  // buffer sizes (limbs / entries), for checked builds
@@ -112,6 +115,9 @@ void choose_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc, int *up
 int choose_levels(int W, int gap);  // Karatsuba depth of least modelled update cost
 int colsum_width(const SubProb *sub, int nsub, int uc);
 cudaError_t launch_update(const UpdParams &p, cudaStream_t s);
+// One block waits (bounded by wait_ns, 0 = default) on an mbarrier that nothing
+// arrives at, with the update kernel's wait routine; records the timeout in st.
+cudaError_t launch_wait_selftest(DevStatus *st, long long wait_ns, cudaStream_t s);
 // INT8 tensor-core (mma.sync u8) form of the FACTOR update, plain entries
 cudaError_t launch_update_i8(const UpdParams &p, cudaStream_t s);
 size_t update_i8_smem(int W);

@@ -79,13 +79,14 @@ HK_DEV unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// bounded wait (about WAIT_LIMIT_NS); false when the limit ran out
-HK_DEV bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// bounded wait (about `limit` ns, at most SPIN_LIMIT polls); false when the
+// limit ran out
+HK_DEV bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (long long i = 0; i < SPIN_LIMIT; i++) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63) == 0 && global_ns() - t0 > WAIT_LIMIT_NS) return false;
+    if ((i & 63) == 0 && global_ns() - t0 > limit) return false;
   }
   return false;
 }
@@ -160,18 +161,20 @@ HK_DEV void decode_output(const UpdParams &p, int o, int *oi, int *oj, long long
 template <int UC>
 __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const __grid_constant__ UpdParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int NS = p.nst;
+  const unsigned long long wlim = p.wait_ns > 0 ? (unsigned long long)p.wait_ns : WAIT_LIMIT_NS;
   const int XPADR = xpadr(p.upc), YPADL = ypadl(UC, p.upc), YPADR = ypadr(UC);
   const int Xsz = ((p.cx + XPADR + 3) / 4) * 4;
   const int Ysz = ((YPADL + p.cy + YPADR + 3) / 4) * 4;
   uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw);
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)USTAGES * (Xsz + Ysz) * 4);
-  uint64_t *empty = full + USTAGES;
-  int *sneg = reinterpret_cast<int *>(empty + USTAGES);  // sign of the stage's product
-  volatile int *abort_flag = sneg + USTAGES;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)NS * (Xsz + Ysz) * 4);
+  uint64_t *empty = full + NS;
+  int *sneg = reinterpret_cast<int *>(empty + NS);  // sign of the stage's product
+  volatile int *abort_flag = sneg + NS;
 
   if (block_status(p.st) != ST_OK) return;  // an earlier step failed: nothing to do
-  if (!HK_CHECK(p.st, (size_t)USTAGES * (Xsz + Ysz) * 4 + 2 * USTAGES * 8 + 4 * (USTAGES + 4) <= dynamic_smem_bytes(),
-                1, (size_t)USTAGES * (Xsz + Ysz) * 4, dynamic_smem_bytes()))
+  if (!HK_CHECK(p.st, (size_t)NS * (Xsz + Ysz) * 4 + 2 * NS * 8 + 4 * (NS + 4) <= dynamic_smem_bytes(),
+                1, (size_t)NS * (Xsz + Ysz) * 4, dynamic_smem_bytes()))
     return;
 
   const int o = blockIdx.y;
@@ -186,7 +189,7 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
   if (nt <= 0) return;
 
   // zero the pads of the stages in use (TMA writes only the operand entries)
-  const int used = min(nt, USTAGES);
+  const int used = min(nt, NS);
   for (int s = 0; s < used; s++) {
     uint32_t *xs = bufs + (size_t)s * (Xsz + Ysz);
     for (int k = threadIdx.x; k < Xsz - p.cx; k += blockDim.x) xs[p.cx + k] = 0;
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
     for (int k = threadIdx.x; k < Ysz - YPADL - p.cy; k += blockDim.x) ys[YPADL + p.cy + k] = 0;
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < USTAGES; s++) {
+    for (int s = 0; s < NS; s++) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], UNT / 32);
     }
@@ -216,10 +219,10 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
     if (lane == 0) {
       int issued = 0;
       for (int it = 0; it < nt; it++) {
-        const int s = it % USTAGES;
-        if (it >= USTAGES) {
-          if (!mbar_wait(&empty[s], ((it / USTAGES) - 1) & 1)) {
-            atomicAdd(&p.st->timeout, 1);
+        const int s = it % NS;
+        if (it >= NS) {
+          if (!mbar_wait(&empty[s], ((it / NS) - 1) & 1, wlim)) {
+            raise_timeout(p.st);
             *abort_flag = 1;
             break;
           }
@@ -254,8 +257,8 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
       }
       if (*abort_flag) {
         // wait (bounded) for our own copies in flight before leaving
-        for (int it = max(0, issued - USTAGES); it < issued; it++)
-          mbar_wait(&full[it % USTAGES], (it / USTAGES) & 1);
+        for (int it = max(0, issued - NS); it < issued; it++)
+          mbar_wait(&full[it % NS], (it / NS) & 1, wlim);
       }
     }
     return;
@@ -290,9 +293,9 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
   for (int m = 0; m < UC; m++) c0[m] = c1[m] = c2[m] = 0;
 
   for (int it = 0; it < nt; it++) {
-    const int s = it % USTAGES;
-    if (!mbar_wait(&full[s], (it / USTAGES) & 1)) {
-      if (lane == 0) atomicAdd(&p.st->timeout, 1);
+    const int s = it % NS;
+    if (!mbar_wait(&full[s], (it / NS) & 1, wlim)) {
+      if (lane == 0) raise_timeout(p.st);
       *abort_flag = 1;
       break;
     }
@@ -355,6 +358,24 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
 #pragma unroll
     for (int m = 0; m < UC + 2; m++)
       if (v[m] != 0 && m < lim) atomicAdd(dst + m, (unsigned long long)(sg * v[m]));
+  }
+}
+
+// Failure-detection self-test: one block arms an mbarrier for a transaction
+// that never comes (no copy is issued, nothing arrives) and waits on it with
+// the same bounded routine as the update kernel.  The wait runs out after the
+// limit, the block records the timeout and returns; nothing hangs and no
+// fault is raised.
+__global__ void k_wait_selftest(DevStatus *st, long long wait_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long lim = wait_ns > 0 ? (unsigned long long)wait_ns : WAIT_LIMIT_NS;
+    if (!mbar_wait(&bar, 0, lim)) raise_timeout(st);
   }
 }
 
@@ -621,14 +642,26 @@ template <int UCT>
 cudaError_t launch_uc(const UpdParams &p, cudaStream_t s) {
   const int Xsz = ((p.cx + xpadr(p.upc) + 3) / 4) * 4;
   const int Ysz = ((ypadl(UCT, p.upc) + p.cy + ypadr(UCT) + 3) / 4) * 4;
-  const size_t smem = (size_t)USTAGES * (Xsz + Ysz) * 4 + 2 * USTAGES * 8 + 4 * (USTAGES + 4);
+  // pipeline depth: the configured ring (HK_USTAGES, default USTAGES); a ring
+  // deeper than the default shrinks (not below it) until three blocks still
+  // fit in an SM's shared memory
+  static const int want = [] {
+    const char *e = getenv("HK_USTAGES");
+    return e ? std::max(2, std::min(USTAGES_MAX, atoi(e))) : USTAGES;
+  }();
+  const size_t stage = (size_t)(Xsz + Ysz) * 4 + 8 * 2 + 4;
+  int nst = want;
+  while (nst > USTAGES && nst * stage + 64 > 72 * 1024) nst--;
+  UpdParams q = p;
+  q.nst = nst;
+  const size_t smem = (size_t)nst * (Xsz + Ysz) * 4 + 2 * nst * 8 + 4 * (nst + 4);
   if (smem > 48 * 1024) {
     cudaError_t e = allow_dynamic_smem((const void *)k_update<UCT>);
     if (e != cudaSuccess) return e;
   }
   const int nz = (p.t1 - p.t0 + p.tchunk - 1) / p.tchunk;
   dim3 grid((p.nunits + UNT - 1) / UNT, p.nout, nz);
-  k_update<UCT><<<grid, UNT + 32, smem, s>>>(p);
+  k_update<UCT><<<grid, UNT + 32, smem, s>>>(q);
   const cudaError_t e = cudaGetLastError();
 #ifdef HK_CHECKED
   if (e != cudaSuccess)
@@ -639,6 +672,11 @@ cudaError_t launch_uc(const UpdParams &p, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t launch_wait_selftest(DevStatus *st, long long wait_ns, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(st, wait_ns);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_update(const UpdParams &p, cudaStream_t s) {
   if (p.nout <= 0 || p.t1 <= p.t0 || p.nunits <= 0) return cudaSuccess;

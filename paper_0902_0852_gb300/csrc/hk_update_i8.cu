@@ -29,7 +29,7 @@ constexpr unsigned long long I8_WAIT_NS = 2000000000ull;
 
 HK_DEV uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-HK_DEV bool i8_wait(uint64_t *bar, uint32_t parity) {
+HK_DEV bool i8_wait(uint64_t *bar, uint32_t parity, unsigned long long limit) {
   unsigned long long t0;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
   for (long long i = 0; i < (1LL << 30); i++) {
@@ -44,7 +44,7 @@ HK_DEV bool i8_wait(uint64_t *bar, uint32_t parity) {
     if ((i & 63) == 0) {
       unsigned long long t;
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-      if (t - t0 > I8_WAIT_NS) return false;
+      if (t - t0 > limit) return false;
     }
   }
   return false;
@@ -133,10 +133,11 @@ __global__ void __launch_bounds__(I8_NT) k_update_i8(const __grid_constant__ Upd
             : "memory");
         sg[n] = p.Asign[ja];
       }
-      if (!i8_wait(bar, it & 1)) {
-        atomicAdd(&p.st->timeout, 1);
+      const unsigned long long lim = p.wait_ns > 0 ? (unsigned long long)p.wait_ns : I8_WAIT_NS;
+      if (!i8_wait(bar, it & 1, lim)) {
+        raise_timeout(p.st);
         sg[10] = 1;
-        i8_wait(bar, it & 1);  // bounded second wait for the copies in flight
+        i8_wait(bar, it & 1, lim);  // bounded second wait for the copies in flight
       }
     }
     __syncthreads();

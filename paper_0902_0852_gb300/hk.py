@@ -29,7 +29,7 @@ EXPORTS = [
     "hk_probe_int_peaks", "hk_mp_op_noalloc", "hk_set_update_path",
     "hk_set_option", "hk_batch_solve",
     "hk_mlp_workspace_bytes", "hk_mlp_forward", "hk_mlp_loss_grad", "hk_mlp_adam", "hk_mlp_train",
-    "hk_set_predictor", "hk_predict", "hk_update_plan",
+    "hk_set_predictor", "hk_predict", "hk_update_plan", "hk_selftest_wait",
 ]
 
 
@@ -85,6 +85,7 @@ def lib():
         L.hk_set_predictor.argtypes = [vp, vp, vp]
         L.hk_predict.argtypes = [vp, i32, vp, vp, vp]
         L.hk_update_plan.argtypes = [i32, i32, P64, P32, P32, P32, P32, i64, P32]
+        L.hk_selftest_wait.argtypes = [vp]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype if name in ("hk_destroy", "hk_strerror") else i32
         L.hk_mlp_workspace_bytes.restype = sz
@@ -297,11 +298,18 @@ def hk_mp_op_noalloc(op, L, x, ex, y, ey, out, eo, stream=None):
                                   ctypes.c_void_p(s)), "hk_mp_op_noalloc")
 
 
-HK_OPT_UPDATE_PATH, HK_OPT_KARATSUBA, HK_OPT_GRAPH, HK_OPT_AUTOTUNE, HK_OPT_PANEL_ROWS, HK_OPT_MAX_ITERS = range(6)
+(HK_OPT_UPDATE_PATH, HK_OPT_KARATSUBA, HK_OPT_GRAPH, HK_OPT_AUTOTUNE, HK_OPT_PANEL_ROWS, HK_OPT_MAX_ITERS,
+ HK_OPT_WAIT_NS) = range(7)
 
 
 def hk_set_option(ctx, option, value):
     _check(lib().hk_set_option(ctx, option, int(value)), "hk_set_option")
+
+
+def hk_selftest_wait(ctx):
+    """Status of the bounded-wait self-test (HK_ERR_TIMEOUT when the wait ran
+    out as designed); returned, not raised."""
+    return lib().hk_selftest_wait(ctx)
 
 
 def hk_batch_solve(ctx, instances, iters=0, nthreads=16):

@@ -80,6 +80,7 @@ def test_every_entry_point_rejects_a_null_context_or_bad_argument(lib):
         lambda: lib.hk_probe_int_peaks(0, None, 0),
         lambda: lib.hk_mlp_forward(None, None, 0, None, None),
         lambda: lib.hk_update_plan(0, -1, None, None, None, None, None, 0, None),
+        lambda: lib.hk_selftest_wait(None),
     ]
     for k, call in enumerate(calls):
         assert call() == ARG, k

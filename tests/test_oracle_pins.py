@@ -483,3 +483,13 @@ def test_golden_beta1_digest_is_the_closed_form():
     N, P = g["N"], g["P"]
     R = [[H.rne(factorial(j) * comb(j, t), 0, P) for j in range(t, N)] for t in range(N)]
     assert mg.digest_R(R, P) == g["R_sha256"]
+
+
+@pytest.mark.parametrize("N,P", [(1, 32), (4, 32), (24, 256), (64, 2048)])
+def test_factorial_factor_is_the_oracles_cholesky(N, P):
+    """The written-out beta = 1 factor (used where the O(N^3) oracle is too
+    slow, N = 1000) equals the oracle's own factorisation wherever P makes
+    every step exact, and refuses a P that does not."""
+    assert H.cholesky_factorial(N, P) == H.cholesky(inputs.moments(N, (1, 1), P), N, P)
+    with pytest.raises(ValueError):
+        H.cholesky_factorial(64, 512)  # 126! has 703 bits
