@@ -40,6 +40,7 @@ def digest_R(R, P):
 
 def main():
     import oracle
+    sys.set_int_max_str_digits(0)  # mantissas of up to 32768 bits as decimal strings
     from paper_0902_0852_gb300 import inputs
     workers = int(sys.argv[1]) if len(sys.argv) > 1 else (os.cpu_count() or 1)
     only = set(sys.argv[2:])

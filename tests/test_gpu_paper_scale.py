@@ -50,3 +50,69 @@ def test_paper_scale_R_closed_form_and_lambda():
     cond = math.lgamma(1999) / math.log(10) - lg
     ce = math.floor(cond)
     assert round(10 ** (cond - ce), 2) == 7.62 and ce == 5780
+
+
+def _dec(lam):
+    n, e = lam
+    lg = math.log10(abs(n)) + e * math.log10(2)
+    ex = math.floor(lg)
+    return round(10 ** (lg - ex), 4), ex
+
+
+def test_paper_scale_lambda_history_bit_exact():
+    """N = 1000, beta = 1, P = 24576, T = 3 steps from the all-ones vector:
+    the R digest and lambda_1..lambda_3 equal the stored oracle values
+    (tests/golden/make_golden.py, written from oracle/ only)."""
+    import json
+    import os
+    import sys
+    from paper_0902_0852_gb300 import build, hk
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, "golden", "paper_scale_beta1.json")
+    with open(path) as f:
+        g = json.load(f)
+    sys.path.insert(0, os.path.join(here, "golden"))
+    from make_golden import digest_R
+    build.build()
+    N, P, T = g["N"], g["P"], g["T"]
+    m = inputs.moments(N, (1, 1), P)
+    with hk.Hankel(0) as h:
+        h.load(N, (1, 1), P, m)
+        h.factor()
+        sign, exp, limbs = hk.hk_get_R_flat(h.ctx, N, P)
+        lam, used = h.smallest_eig(T)
+        hist = h.history(used)
+    vals = hk.unpack(sign, exp, limbs)
+    rows, k = [], 0
+    for t in range(N):
+        rows.append(vals[k:k + N - t])
+        k += N - t
+    assert digest_R(rows, P) == g["R_sha256"]
+    assert used == T
+    sys.set_int_max_str_digits(0)  # 24576-bit mantissas as decimal strings
+    assert [[str(n), e] for n, e in hist] == g["history"]
+
+
+def test_paper_scale_beta_7_4_rows_and_table3():
+    """N = 1000, beta = 7/4, P = 24576 (Table 3: lambda_min = 3.6209e-246):
+    full-width rows of the device factor -- the first, both sides of the first
+    panel-block edge, both sides of the middle, the last -- equal the oracle's
+    row routine applied to the device's own rows above them, bit for bit, and
+    the converged lambda_min matches Table 3 to its five figures."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from rowcheck import check_rows_flat
+    from paper_0902_0852_gb300 import build, hk
+    build.build()
+    N, P, beta = 1000, 24576, (7, 4)
+    m = inputs.moments(N, beta, P)
+    with hk.Hankel(0) as h:
+        h.load(N, beta, P, m)
+        h.factor()
+        sign, exp, limbs = hk.hk_get_R_flat(h.ctx, N, P)
+        lam, used = h.smallest_eig(0)
+    assert _dec(lam) == (3.6209, -246), (_dec(lam), used)
+    workers = min(16, os.cpu_count() or 1)
+    bad = check_rows_flat(m, sign, exp, limbs, N, P, [0, 15, 16, 499, 500, 999], workers)
+    assert bad == [], bad[:10]
