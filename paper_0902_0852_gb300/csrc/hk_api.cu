@@ -135,6 +135,23 @@ struct hk_ctx {
   int resumes = 0;  // widenings that resumed at a later block instead of restarting
   long long top_margin = 0;  // extra bits above the a priori column bounds
   bool timing = true;
+  // shifted LDL^T of M - xI (the paper's determinant), Secant and verification
+  bool ldl_mode = false;     // the factor driver runs the LDL^T instead of Cholesky
+  Arena ldl_arena, ldl_small;
+  MpArr Qf{};                // CDivDiag in floating form
+  uint32_t *B = nullptr, *Bexp = nullptr;  // aligned (and expanded) CDivDiag
+  int32_t *Bsign = nullptr;
+  long long *hrow = nullptr;  // row shifts h_t
+  MpArr ldl_x{}, ldl_det{};  // the shift and the determinant (one entry each)
+  int *ldl_cnt = nullptr;    // [0] negative pivots, [1] first zero pivot
+  int ldl_N = 0, ldl_L = 0, ldl_W = 0, ldl_levels = -1, ldl_sL = 0;
+  int ldl_xzero = 1;
+  bool ldl_ready = false;    // R slots hold the last LDL^T (hk_get_ldlt_flat)
+  Arena sec_arena;
+  MpArr sec_x{}, sec_p{}, sec_t{};  // iterates, determinants, scratch values
+  void *sec_work = nullptr;
+  int *sec_flags = nullptr;
+  int sec_cap = 0, sec_L = 0, sec_count = 0;
 };
 
 namespace {
@@ -293,8 +310,8 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
     cudaEventCreate(&e1);
   }
   float best = 1e30f;
-  const int ucs[3] = {7, 9, 11};
-  for (int ui = 0; ui < 3 && ok; ui++) {
+  const int ucs[4] = {7, 8, 9, 11};
+  for (int ui = 0; ui < 4 && ok; ui++) {
     const int uc = ucs[ui];
     for (int upc = 2 * uc; upc <= 8 * uc && upc <= upc_cap && ok; upc += uc) {
       const int n = build_units(sub, nsub, uc, upc, nullptr, 0);
@@ -564,8 +581,22 @@ int factor_attempt(hk_ctx *c, int r_start) {
     c->fac_W = W;
     c->fac_levels = levels;
   }
+  if (c->ldl_mode && (c->ldl_N != N || c->ldl_L != L || c->ldl_W != W || c->ldl_levels != levels)) {
+    c->ldl_arena.release();
+    c->ldl_N = c->ldl_L = c->ldl_W = 0;
+    CK(alloc_mp(c, c->ldl_arena, &c->Qf, NT, L));
+    CK(alloc(c, c->ldl_arena, &c->B, NT * (size_t)W));
+    CK(alloc(c, c->ldl_arena, &c->Bsign, NT));
+    CK(alloc(c, c->ldl_arena, &c->hrow, (size_t)N));
+    c->Bexp = nullptr;
+    if (levels > 0) CK(alloc(c, c->ldl_arena, &c->Bexp, NT * (size_t)c->kl.stride));
+    c->ldl_N = N;
+    c->ldl_L = L;
+    c->ldl_W = W;
+    c->ldl_levels = levels;
+  }
   CK(reset_status(c));
-  if (!c->use_graph) return factor_enqueue(c, sc, r_start);
+  if (!c->use_graph || c->ldl_mode) return factor_enqueue(c, sc, r_start);
   // capture the whole launch sequence of this factorisation in a CUDA graph
   // and replay it (no host synchronisation happens inside the sequence)
   const bool timing = c->timing;
@@ -650,6 +681,27 @@ int factor_enqueue(hk_ctx *c, const Sched &sc, int r_start) {
   const long long cta_per_out = (sc.n + UNT - 1) / UNT;
   const long long target = 6LL * sm_count(c) * 3;
 
+  LdlParams lq;
+  std::memset(&lq, 0, sizeof(lq));
+  if (c->ldl_mode) {
+    lq.pp = pp;
+    lq.Q = c->Qf;
+    lq.B = c->B;
+    lq.Bsign = c->Bsign;
+    lq.Bexp = c->Bexp;
+    lq.h = c->hrow;
+    lq.x = c->ldl_x;
+    lq.xzero = c->ldl_xzero;
+    lq.det = c->ldl_det;
+    lq.negcount = c->ldl_cnt;
+    lq.zero_row = c->ldl_cnt + 1;
+    up.mode = M_LDLT;
+    up.B = levels > 0 ? c->Bexp : c->B;
+    up.Bsign = c->Bsign;
+    const int init[2] = {0, INT_MAX};
+    CK(cudaMemcpyAsync(c->ldl_cnt, init, sizeof(init), cudaMemcpyHostToDevice, c->stream));
+    r_start = 0;  // an LDL^T restarts after a widening (no re-alignment of its two triangles)
+  }
   if (r_start > 0) {
     CK(launch_realign(pp, r_start, c->stream));
     DBG(c, "realign", r_start, W);
@@ -669,17 +721,25 @@ int factor_enqueue(hk_ctx *c, const Sched &sc, int r_start) {
       up.t1 = r0;
       up.tchunk = pick_tchunk(r0, cta_per_out * nout, target);
       ev_begin(c, 0);
-      CK(c->update_path == 1 ? launch_update_i8(up, c->stream) : launch_update(up, c->stream));
+      CK((c->update_path == 1 && !c->ldl_mode) ? launch_update_i8(up, c->stream) : launch_update(up, c->stream));
       DBG(c, "factor update", up.ra, up.t1);
       ev_end(c);
       c->launches++;
     }
     for (int i = r0; i < r1; i++) {
       ev_begin(c, 1);
-      CK(launch_diag(pp, i, c->stream));
-      DBG(c, "diag", i, 0);
-      CK(launch_offdiag(pp, i, c->stream));
-      DBG(c, "offdiag", i, 0);
+      if (c->ldl_mode) {
+        lq.pp.r0 = r0;
+        CK(launch_ldl_pivot(lq, i, c->stream));
+        DBG(c, "ldl pivot", i, 0);
+        CK(launch_ldl_row(lq, i, c->stream));
+        DBG(c, "ldl row", i, 0);
+      } else {
+        CK(launch_diag(pp, i, c->stream));
+        DBG(c, "diag", i, 0);
+        CK(launch_offdiag(pp, i, c->stream));
+        DBG(c, "offdiag", i, 0);
+      }
       ev_end(c);
       c->launches += (i + 1 < N) ? 2 : 1;
       if (i + 1 < r1) {
@@ -690,7 +750,7 @@ int factor_enqueue(hk_ctx *c, const Sched &sc, int r_start) {
         up.t1 = i + 1;
         up.tchunk = 1;
         ev_begin(c, 0);
-        CK(c->update_path == 1 ? launch_update_i8(up, c->stream) : launch_update(up, c->stream));
+        CK((c->update_path == 1 && !c->ldl_mode) ? launch_update_i8(up, c->stream) : launch_update(up, c->stream));
         DBG(c, "factor update", up.ra, up.t1);
         ev_end(c);
         c->launches++;
@@ -1103,6 +1163,9 @@ void hk_destroy(hk_ctx *c) {
   c->sol_arena.release();
   c->fac_arena.release();
   c->res_arena.release();
+  c->ldl_arena.release();
+  c->ldl_small.release();
+  c->sec_arena.release();
   c->base_arena.release();
   if (c->pred_params) cudaFree(c->pred_params);
   if (c->pred_buf) cudaFree(c->pred_buf);
@@ -1206,6 +1269,14 @@ int hk_load_moments_flat(hk_ctx *c, int N, int bnum, int bden, int P, const int3
     c->vecAexp_cap = 0;
     c->colsum_s_cap = 0;
     c->fac_N = c->fac_L = c->fac_W = 0;
+    c->ldl_arena.release();
+    c->ldl_small.release();
+    c->sec_arena.release();
+    c->ldl_N = c->ldl_L = c->ldl_W = 0;
+    c->ldl_sL = 0;
+    c->ldl_x = MpArr{};
+    c->sec_cap = c->sec_L = c->sec_count = 0;
+    c->ldl_ready = false;
     c->mom = MpArr{};
     c->N = N;
     c->L = L;
@@ -1222,6 +1293,8 @@ int hk_load_moments_flat(hk_ctx *c, int N, int bnum, int bden, int P, const int3
   CK(cudaMemcpyAsync(c->mom.limbs, limbs, sizeof(uint32_t) * (size_t)M * L, kind, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->loaded = true;
+  c->ldl_ready = false;
+  c->sec_count = 0;
   return HK_OK;
 }
 
@@ -1240,11 +1313,14 @@ int hk_load_moments(hk_ctx *c, int N, int bnum, int bden, int P, const hk_mp *mo
   return hk_load_moments_flat(c, N, bnum, bden, P, s.data(), e.data(), l.data(), 0);
 }
 
-int hk_factor(hk_ctx *c, int *bad_row) {
-  if (!c) return HK_ERR_ARG;
-  if (!c->loaded) return HK_ERR_STATE;
+}  // extern "C"
+
+// The blocked factorisation with its window widenings: the Cholesky of M, or
+// (c->ldl_mode) the shifted LDL^T of M - xI.
+static int factor_run(hk_ctx *c, int *bad_row) {
   cudaSetDevice(c->device);
   c->factored = false;
+  c->ldl_ready = false;
   c->launches = 0;
   c->widenings = 0;
   c->resumes = 0;
@@ -1254,7 +1330,8 @@ int hk_factor(hk_ctx *c, int *bad_row) {
   long long slack = c->N + 128;
   if (const char *e = getenv("HK_WINDOW_SLACK")) slack = std::max(0LL, atoll(e));
   c->W = round4(c->L + (slack + 31) / 32);
-  c->top_margin = 0;
+  // the LDL^T operands are the Cholesky factor's within a factor of two
+  c->top_margin = c->ldl_mode ? 2 : 0;
   if (const char *e = getenv("HK_NB")) c->nb = std::max(1, atoi(e));  // panel block rows (tuning)
   if (const char *e = getenv("HK_KARATSUBA")) c->kar_levels = std::min(MAX_KAR, std::max(-1, atoi(e)));  // (tuning)
   cudaEvent_t e0, e1;
@@ -1296,7 +1373,7 @@ int hk_factor(hk_ctx *c, int *bad_row) {
       c->widenings++;
       const int row = st.range_row;
       r_start = (row != INT_MAX && row >= 0 && row < c->N) ? (row / c->nb) * c->nb : 0;
-      if (r_start > 0 && c->use_graph) r_start = 0;  // graphs record whole factorisations
+      if (r_start > 0 && (c->use_graph || c->ldl_mode)) r_start = 0;  // whole factorisations only
       if (r_start > 0) c->resumes++;
       continue;
     }
@@ -1305,17 +1382,29 @@ int hk_factor(hk_ctx *c, int *bad_row) {
       result = HK_ERR_NOT_PD;
       break;
     }
-    if (st.code != ST_OK) {  // a failed device check
+    if (st.code != ST_OK && !(c->ldl_mode && st.code == ST_ZERO)) {  // a failed device check
       result = HK_ERR_CUDA;
       break;
     }
-    c->factored = true;
+    if (c->ldl_mode)
+      c->ldl_ready = true;  // a zero pivot is a result (det = 0), not an error
+    else
+      c->factored = true;
     result = HK_OK;
     break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return result;
+}
+
+extern "C" {
+
+int hk_factor(hk_ctx *c, int *bad_row) {
+  if (!c) return HK_ERR_ARG;
+  if (!c->loaded) return HK_ERR_STATE;
+  c->ldl_mode = false;
+  return factor_run(c, bad_row);
 }
 
 int hk_selftest_wait(hk_ctx *c) {
@@ -1638,6 +1727,240 @@ int hk_predict(hk_ctx *c, int count, const double *N, const double *beta, float 
     out3[3 * k + 2] = (float)std::exp2(t2);    // log2(iterations)
   }
   return HK_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// The paper's own method: P(x) = det(M - xI) by the shifted LDL^T, the Secant
+// recurrence on it, and the inertia on both sides of the root
+// ---------------------------------------------------------------------------
+namespace {
+
+cudaError_t ensure_ldl_small(hk_ctx *c) {
+  if (c->ldl_sL == c->L && c->ldl_x.limbs) return cudaSuccess;
+  c->ldl_small.release();
+  c->ldl_sL = 0;
+  cudaError_t e = alloc_mp(c, c->ldl_small, &c->ldl_x, 1, c->L);
+  if (e == cudaSuccess) e = alloc_mp(c, c->ldl_small, &c->ldl_det, 1, c->L);
+  if (e == cudaSuccess) e = alloc(c, c->ldl_small, &c->ldl_cnt, 2);
+  if (e == cudaSuccess) c->ldl_sL = c->L;
+  return e;
+}
+
+cudaError_t copy_entry(MpArr dst, int kd, MpArr src, int ks, int L, cudaMemcpyKind kind, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(dst.limbs + (size_t)kd * L, src.limbs + (size_t)ks * L, 4 * (size_t)L, kind, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst.sign + kd, src.sign + ks, 4, kind, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst.exp + kd, src.exp + ks, 8, kind, s);
+  return e;
+}
+
+// the shifted LDL^T with x = xs[kx] (device); its determinant into dst[kd]
+int ldlt_dev(hk_ctx *c, MpArr xs, int kx, MpArr dst, int kd) {
+  CK(ensure_ldl_small(c));
+  CK(copy_entry(c->ldl_x, 0, xs, kx, c->L, cudaMemcpyDeviceToDevice, c->stream));
+  c->ldl_xzero = 0;
+  c->ldl_mode = true;
+  const int rc = factor_run(c, nullptr);
+  c->ldl_mode = false;
+  if (rc != HK_OK) return rc;
+  if (dst.limbs) CK(copy_entry(dst, kd, c->ldl_det, 0, c->L, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return HK_OK;
+}
+
+int read_counts(hk_ctx *c, int *neg, int *zero_row) {
+  int h[2] = {0, INT_MAX};
+  CK(cudaMemcpyAsync(h, c->ldl_cnt, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (neg) *neg = h[0];
+  if (zero_row) *zero_row = h[1] == INT_MAX ? -1 : h[1];
+  return HK_OK;
+}
+
+// sign of the determinant held in ldl_det: 1, -1, or 0 (zero)
+int det_sign(hk_ctx *c, int *sgn) {
+  std::vector<uint32_t> l(c->L);
+  int32_t sg = 0;
+  CK(cudaMemcpyAsync(l.data(), c->ldl_det.limbs, 4 * (size_t)c->L, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&sg, c->ldl_det.sign, 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  bool z = true;
+  for (uint32_t v : l) z &= v == 0;
+  *sgn = z ? 0 : (sg ? -1 : 1);
+  return HK_OK;
+}
+
+bool mp_ok(const hk_mp *v) { return v && v->limbs && (v->sign == 0 || v->sign == 1); }
+
+}  // namespace
+
+extern "C" {
+
+int hk_ldlt_det(hk_ctx *c, const hk_mp *x, hk_mp *det, int *neg_pivots, int *zero_row) {
+  if (!c || !mp_ok(x) || !det || !det->limbs) return HK_ERR_ARG;
+  if (!c->loaded) return HK_ERR_STATE;
+  cudaSetDevice(c->device);
+  CK(ensure_ldl_small(c));
+  const int L = c->L;
+  bool z = true;
+  for (int l = 0; l < L; l++) z &= x->limbs[l] == 0;
+  if (!z && !(x->limbs[L - 1] >> 31)) return HK_ERR_ARG;  // not normalised
+  const int32_t sg = z ? 0 : x->sign;
+  const long long ex = z ? 0 : x->exp;
+  CK(cudaMemcpyAsync(c->ldl_x.limbs, x->limbs, 4 * (size_t)L, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->ldl_x.sign, &sg, 4, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->ldl_x.exp, &ex, 8, cudaMemcpyHostToDevice, c->stream));
+  c->ldl_xzero = z ? 1 : 0;
+  c->ldl_mode = true;
+  const int rc = factor_run(c, nullptr);
+  c->ldl_mode = false;
+  if (rc != HK_OK) return rc;
+  int32_t dsg = 0;
+  long long dex = 0;
+  CK(cudaMemcpyAsync(det->limbs, c->ldl_det.limbs, 4 * (size_t)L, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&dsg, c->ldl_det.sign, 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&dex, c->ldl_det.exp, 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  det->sign = dsg;
+  det->exp = dex;
+  return read_counts(c, neg_pivots, zero_row);
+}
+
+int hk_get_ldlt_flat(hk_ctx *c, int which, int32_t *sign, int64_t *exp, uint32_t *limbs) {
+  if (!c || which < 0 || which > 2 || !sign || !exp || !limbs) return HK_ERR_ARG;
+  if (!c->ldl_ready) return HK_ERR_STATE;
+  const int N = c->N, L = c->L;
+  const size_t NT = (size_t)N * (N + 1) / 2;
+  if (which == 0) {
+    for (int t = 0; t < N; t++) {
+      const size_t k = tri_idx(t, t, N);
+      CK(cudaMemcpyAsync(limbs + (size_t)t * L, c->R.limbs + k * L, 4 * (size_t)L, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaMemcpyAsync(sign + t, c->R.sign + k, 4, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaMemcpyAsync(exp + t, c->R.exp + k, 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+  } else {
+    const MpArr &m = which == 1 ? c->R : c->Qf;
+    CK(cudaMemcpyAsync(limbs, m.limbs, 4 * NT * L, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(sign, m.sign, 4 * NT, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(exp, m.exp, 8 * NT, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if (which == 2)  // CDivDiag has no diagonal entries
+    for (int t = 0; t < N; t++) {
+      const size_t k = tri_idx(t, t, N);
+      sign[k] = 0;
+      exp[k] = 0;
+      std::memset(limbs + k * L, 0, 4 * (size_t)L);
+    }
+  return HK_OK;
+}
+
+int hk_secant(hk_ctx *c, int max_steps, hk_mp *root, int *dets_used) {
+  if (!c || max_steps < 0 || max_steps > 10000 || !root || !root->limbs) return HK_ERR_ARG;
+  if (!c->loaded) return HK_ERR_STATE;
+  cudaSetDevice(c->device);
+  const int L = c->L, N = c->N;
+  const int cap = max_steps + 3;
+  if (c->sec_cap < cap || c->sec_L != L) {
+    c->sec_arena.release();
+    c->sec_cap = c->sec_L = 0;
+    CK(alloc_mp(c, c->sec_arena, &c->sec_x, cap, L));
+    CK(alloc_mp(c, c->sec_arena, &c->sec_p, cap, L));
+    CK(alloc_mp(c, c->sec_arena, &c->sec_t, 5, L));
+    CK(alloc(c, c->sec_arena, reinterpret_cast<unsigned char **>(&c->sec_work), scalar_work_bytes(L)));
+    CK(alloc(c, c->sec_arena, &c->sec_flags, 4));
+    c->sec_cap = cap;
+    c->sec_L = L;
+  }
+  c->sec_count = 0;
+  // x_2 = 0: P(0) = det M, whose pivots give x_1 = -min_t D_t
+  CK(cudaMemsetAsync(c->sec_x.limbs + L, 0, 4 * (size_t)L, c->stream));
+  CK(cudaMemsetAsync(c->sec_x.sign + 1, 0, 4, c->stream));
+  CK(cudaMemsetAsync(c->sec_x.exp + 1, 0, 8, c->stream));
+  int rc = ldlt_dev(c, c->sec_x, 1, c->sec_p, 1);
+  if (rc != HK_OK) return rc;
+  CK(launch_neg_min_pivot(c->R, N, L, c->sec_x, 0, c->stream));
+  rc = ldlt_dev(c, c->sec_x, 0, c->sec_p, 0);
+  if (rc != HK_OK) return rc;
+  int count = 2, have_last = 0;
+  for (int k = 0; k < max_steps; k++) {
+    CK(launch_secant_step(c->sec_x, c->sec_p, c->sec_t, count - 2, count - 1, count, k, have_last, L, c->sec_work,
+                          c->sec_flags, c->stream));
+    int f[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(f, c->sec_flags, sizeof(f), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (f[3]) return HK_ERR_TIMEOUT;  // a correction loop did not settle
+    if (f[0] || f[1]) break;          // no secant, or the step stopped shrinking
+    rc = ldlt_dev(c, c->sec_x, count, c->sec_p, count);
+    if (rc != HK_OK) return rc;
+    count++;
+    CK(copy_entry(c->sec_t, 4, c->sec_t, 3, L, cudaMemcpyDeviceToDevice, c->stream));
+    have_last = 1;
+    if (f[2]) break;  // converged
+  }
+  c->sec_count = count;
+  MpArr host{&root->sign, reinterpret_cast<long long *>(&root->exp), root->limbs};
+  CK(copy_entry(host, 0, c->sec_x, count - 1, L, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (dets_used) *dets_used = count;
+  return HK_OK;
+}
+
+int hk_get_secant_flat(hk_ctx *c, int count, int32_t *xsign, int64_t *xexp, uint32_t *xlimbs, int32_t *psign,
+                       int64_t *pexp, uint32_t *plimbs) {
+  if (!c || count < 0 || !xsign || !xexp || !xlimbs || !psign || !pexp || !plimbs) return HK_ERR_ARG;
+  if (count > c->sec_count) return HK_ERR_STATE;
+  const int L = c->L;
+  for (int k = 0; k < count; k++) {
+    MpArr hx{xsign + k, reinterpret_cast<long long *>(xexp + k), xlimbs + (size_t)k * L};
+    MpArr hp{psign + k, reinterpret_cast<long long *>(pexp + k), plimbs + (size_t)k * L};
+    CK(copy_entry(hx, 0, c->sec_x, k, L, cudaMemcpyDeviceToHost, c->stream));
+    CK(copy_entry(hp, 0, c->sec_p, k, L, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return HK_OK;
+}
+
+int hk_secant_verify(hk_ctx *c, const hk_mp *x, int bits, int P2, int *out4) {
+  if (!c || !mp_ok(x) || !out4 || bits < 1 || bits > 1024 || P2 % 32 || P2 > HK_MAX_P) return HK_ERR_ARG;
+  if (!c->loaded) return HK_ERR_STATE;
+  if ((long long)P2 < (long long)c->P + bits + 1) return HK_ERR_ARG;
+  cudaSetDevice(c->device);
+  const int N = c->N, L = c->L, L2 = P2 / 32, M = 2 * N - 1;
+  bool z = true;
+  for (int l = 0; l < L; l++) z &= x->limbs[l] == 0;
+  if (z || !(x->limbs[L - 1] >> 31)) return HK_ERR_ARG;  // a nonzero, normalised root
+  hk_ctx *c2 = nullptr;
+  int rc = hk_create(&c2, c->device, c->stream);
+  if (rc != HK_OK) return rc;
+  Arena tmp;
+  MpArr wm{}, xt{}, xv{};
+  cudaError_t e = alloc_mp(c, tmp, &wm, M, L2);
+  if (e == cudaSuccess) e = alloc_mp(c, tmp, &xt, 1, L);
+  if (e == cudaSuccess) e = alloc_mp(c, tmp, &xv, 2, L2);
+  if (e == cudaSuccess) e = launch_widen(c->mom, M, L, wm, L2, c->stream);
+  if (e == cudaSuccess) {
+    MpArr hx{const_cast<int32_t *>(&x->sign), reinterpret_cast<long long *>(const_cast<int64_t *>(&x->exp)),
+             const_cast<uint32_t *>(x->limbs)};
+    e = copy_entry(xt, 0, hx, 0, L, cudaMemcpyHostToDevice, c->stream);
+  }
+  if (e == cudaSuccess) e = launch_scale_pm(xt, 0, L, bits, -1, xv, 0, L2, c->stream);
+  if (e == cudaSuccess) e = launch_scale_pm(xt, 0, L, bits, +1, xv, 1, L2, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  rc = e == cudaSuccess ? HK_OK : cuda_status(e);
+  if (rc == HK_OK) rc = hk_load_moments_flat(c2, N, c->bnum, c->bden, P2, wm.sign, reinterpret_cast<int64_t *>(wm.exp),
+                                             wm.limbs, 1);
+  for (int side = 0; side < 2 && rc == HK_OK; side++) {
+    rc = ldlt_dev(c2, xv, side, MpArr{}, 0);
+    int sg = 0;
+    if (rc == HK_OK) rc = read_counts(c2, &out4[side], nullptr);
+    if (rc == HK_OK) rc = det_sign(c2, &sg);
+    out4[2 + side] = sg;
+  }
+  tmp.release();
+  hk_destroy(c2);
+  return rc;
 }
 
 }  // extern "C"

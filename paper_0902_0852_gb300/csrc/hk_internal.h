@@ -35,7 +35,9 @@ struct Unit {
   int p0;  // first p (limb index of the X operand)
 };
 
-enum UpdMode { M_FACTOR = 0, M_GEMV_FWD = 1, M_GEMV_BACK = 2, M_DOT = 3 };
+// M_LDLT: the shifted LDL^T of the paper's determinant -- X from the aligned
+// columns C (A, Asign), Y from the aligned quotients CDivDiag (B, Bsign)
+enum UpdMode { M_FACTOR = 0, M_GEMV_FWD = 1, M_GEMV_BACK = 2, M_DOT = 3, M_LDLT = 4 };
 
 // One integer contraction sum_t X_t[xoff..xoff+wx) * Y_t[yoff..yoff+wy), added
 // to the output's column sums at each (column offset, sign) term.
@@ -70,6 +72,8 @@ struct UpdParams {
   int N;
   const uint32_t *A;       // R entries (plain, or expanded), packed upper triangle
   const int32_t *Asign;
+  const uint32_t *B;       // M_LDLT: the second operand triangle (same layout as A)
+  const int32_t *Bsign;
   int astride;             // limbs per A entry
   const uint32_t *Vx;      // aligned vectors
   const int32_t *Vxsign;
@@ -147,6 +151,30 @@ cudaError_t launch_offdiag(const PanelParams &p, int i, cudaStream_t s);
 cudaError_t launch_realign(const PanelParams &p, int r0, cudaStream_t s);
 size_t panel_smem_diag(int L, int C);
 size_t panel_smem_row(int L, int C);
+
+// ---- shifted LDL^T, Secant and verification (hk_ldlt.cu) ------------------------
+struct LdlParams {
+  PanelParams pp;          // moments, grids, C entries (R slots; D_t on the diagonal), aligned
+                           // and expanded C (A, Aexp), reciprocals of |D_t|, column sums
+  MpArr Q;                 // CDivDiag Q_t[r] in floating form (packed, off-diagonal)
+  uint32_t *B;             // Q aligned on the column grids shifted by -h_t (W limbs)
+  int32_t *Bsign;
+  uint32_t *Bexp;          // Karatsuba expansion of B
+  long long *h;            // row shifts h_t
+  MpArr x;                 // the shift (one entry)
+  int xzero;               // x = 0
+  MpArr det;               // running determinant (one entry)
+  int *negcount;           // negative pivots so far
+  int *zero_row;           // first zero pivot (atomicMin)
+};
+cudaError_t launch_ldl_pivot(const LdlParams &q, int i, cudaStream_t s);
+cudaError_t launch_ldl_row(const LdlParams &q, int i, cudaStream_t s);
+size_t scalar_work_bytes(int L);
+cudaError_t launch_secant_step(MpArr xs, MpArr ps, MpArr tmpv, int k1, int k2, int k3, int kstep, int have_last,
+                               int L, void *work, int *flags, cudaStream_t s);
+cudaError_t launch_neg_min_pivot(MpArr R, int N, int L, MpArr dst, int kd, cudaStream_t s);
+cudaError_t launch_scale_pm(MpArr src, int ks, int L, int bits, int sgn, MpArr dst, int kd, int L2, cudaStream_t s);
+cudaError_t launch_widen(MpArr src, int n, int L, MpArr dst, int L2, cudaStream_t s);
 
 // ---- solve kernels (hk_solve.cu) -------------------------------------------------
 struct SolveParams {

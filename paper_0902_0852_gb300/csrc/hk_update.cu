@@ -44,7 +44,9 @@ namespace hk {
 
 namespace {
 
-__host__ __device__ inline int ypadr(int uc) { return ((uc + 3) / 4) * 4; }
+// right pad of a staged Y entry: a unit reads up to uc + 2 limbs past it (a
+// stripe-8 unit's chunk may start up to three limbs early, see build_units)
+__host__ __device__ inline int ypadr(int uc) { return ((uc + 6) / 4) * 4; }
 __host__ __device__ inline int xpadr(int upc) { return ((upc + 3) / 4) * 4; }
 __host__ __device__ inline int ypadl(int uc, int upc) { return ((uc + upc + 3) / 4) * 4; }
 constexpr long long SPIN_LIMIT = 1LL << 30;
@@ -113,6 +115,12 @@ HK_DEV Operands operands(const UpdParams &p, int oi, int oj, int t) {
     r.x = p.A + ia * p.astride;
     r.y = p.A + ja * p.astride;
     r.neg = p.Asign[ia] ^ p.Asign[ja];
+  } else if (p.mode == M_LDLT) {
+    // C_t[i] * CDivDiag_t[j]: column entry of row t against its quotient
+    const long long ia = tri_idx(t, oi, N), ja = tri_idx(t, oj, N);
+    r.x = p.A + ia * p.astride;
+    r.y = p.B + ja * p.astride;
+    r.neg = p.Asign[ia] ^ p.Bsign[ja];
   } else if (p.mode == M_GEMV_FWD) {
     const long long ia = tri_idx(t, oi, N);
     r.x = p.A + ia * p.astride;
@@ -133,17 +141,32 @@ HK_DEV Operands operands(const UpdParams &p, int oi, int oj, int t) {
 
 // output o -> (i, j) and its row of colsum
 HK_DEV void decode_output(const UpdParams &p, int o, int *oi, int *oj, long long *crow) {
-  if (p.mode == M_FACTOR) {
-    int i = p.ra;
-    long long rem = o;
-    while (rem >= p.N - i) {
-      rem -= p.N - i;
-      i++;
+  if (p.mode == M_FACTOR || p.mode == M_LDLT) {
+    // column-major over the block's outputs: the rows i of one column j are
+    // neighbours in launch order, so the operand entries (t, j) they share are
+    // read from L2 by consecutive blocks (the entries (t, i) of the block's
+    // few rows are shared by all and stay resident)
+    const int n = p.rb - p.ra;
+    const long long tri = (long long)n * (n + 1) / 2;
+    int i, j;
+    if (o < tri) {  // columns j < rb: rows ra .. j
+      int c = 0;
+      long long rem = o;
+      while (rem > c) {
+        rem -= c + 1;
+        c++;
+      }
+      j = p.ra + c;
+      i = p.ra + (int)rem;
+    } else {
+      const long long q = o - tri;
+      j = p.rb + (int)(q / n);
+      i = p.ra + (int)(q % n);
     }
     *oi = i;
-    *oj = i + (int)rem;
+    *oj = j;
     const long long k = i - p.r0;
-    *crow = k * p.N - (k * (i + p.r0 - 1)) / 2 + rem;
+    *crow = k * p.N - (k * (i + p.r0 - 1)) / 2 + (j - i);
   } else if (p.mode == M_DOT) {
     *oi = 0;
     *oj = o;
@@ -218,10 +241,10 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
     // ---------------- producer warp ----------------
     if (lane == 0) {
       int issued = 0;
-      for (int it = 0; it < nt; it++) {
-        const int s = it % NS;
-        if (it >= NS) {
-          if (!mbar_wait(&empty[s], ((it / NS) - 1) & 1, wlim)) {
+      int s = 0, rnd = 0;  // stage of `it` and how often the ring has wrapped
+      for (int it = 0; it < nt; it++, s = (s + 1 == NS) ? 0 : s + 1, rnd += (s == 0)) {
+        if (rnd > 0) {
+          if (!mbar_wait(&empty[s], (rnd - 1) & 1, wlim)) {
             raise_timeout(p.st);
             *abort_flag = 1;
             break;
@@ -233,8 +256,8 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
         {
           const uint32_t *bx = p.mode == M_DOT ? p.Vx : p.A;
           const long long lx = p.mode == M_DOT ? p.vx_len : p.a_len;
-          const uint32_t *by = p.mode == M_FACTOR ? p.A : (p.mode == M_DOT && oj == 0 ? p.Vx : p.Vy);
-          const long long ly = p.mode == M_FACTOR ? p.a_len : (p.mode == M_DOT && oj == 0 ? p.vx_len : p.vy_len);
+          const uint32_t *by = p.mode == M_FACTOR ? p.A : p.mode == M_LDLT ? p.B : (p.mode == M_DOT && oj == 0 ? p.Vx : p.Vy);
+          const long long ly = (p.mode == M_FACTOR || p.mode == M_LDLT) ? p.a_len : (p.mode == M_DOT && oj == 0 ? p.vx_len : p.vy_len);
           const long long ox = op.x + wlo - bx, oy = op.y + wlo - by;
           if (!HK_CHECK(p.st, ox >= 0 && ox + bytesX / 4 <= lx, 2, ox, lx) ||
               !HK_CHECK(p.st, oy >= 0 && oy + bytesY / 4 <= ly, 3, oy, ly) ||
@@ -274,6 +297,9 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
   // checked: a bad entry would index the operand tiles with wrong offsets)
   if (active && sp >= p.nsub) active = check_fail(p.st, 5, sp, p.nsub);
   const int xoff = p.sub[active ? sp : 0].xoff - wlo, yoff = p.sub[active ? sp : 0].yoff - wlo;
+  // stripe-8 units read X four limbs at a time: chunk starts and piece
+  // offsets are multiples of four limbs (always checked)
+  if (UC == 8 && active && ((p0 | xoff) & 3)) active = check_fail(p.st, 10, p0, xoff);
 #ifdef HK_CHECKED
   if (active) {
     // every shared-memory word the unit reads lies in its stage's X or Y tile
@@ -292,9 +318,9 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
 #pragma unroll
   for (int m = 0; m < UC; m++) c0[m] = c1[m] = c2[m] = 0;
 
-  for (int it = 0; it < nt; it++) {
-    const int s = it % NS;
-    if (!mbar_wait(&full[s], (it / NS) & 1, wlim)) {
+  int s = 0, rnd = 0;  // stage of `it` and how often the ring has wrapped
+  for (int it = 0; it < nt; it++, s = (s + 1 == NS) ? 0 : s + 1, rnd += (s == 0)) {
+    if (!mbar_wait(&full[s], rnd & 1, wlim)) {
       if (lane == 0) raise_timeout(p.st);
       *abort_flag = 1;
       break;
@@ -303,7 +329,41 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
     const uint32_t *X = bufs + (size_t)s * (Xsz + Ysz) + xoff;
     const uint32_t *Y = bufs + (size_t)s * (Xsz + Ysz) + Xsz + YPADL + yoff;
     const int neg = sneg[s];
-    if (active) {
+    if (UC == 8 && active) {
+      // X read as aligned quads: two 128-bit shared loads per eight p-steps
+      uint32_t wb[UC];
+#pragma unroll
+      for (int m = 1; m < UC; m++) wb[m] = Y[d0 + m - p0];
+      if (!neg) {
+#pragma unroll 1
+        for (int b = 0; b < p.upc / UC; b++) {
+          const int pb = p0 + b * UC;
+          const uint4 xa = *reinterpret_cast<const uint4 *>(X + pb);
+          const uint4 xb = *reinterpret_cast<const uint4 *>(X + pb + 4);
+          const uint32_t xq[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+          for (int j = 0; j < UC; j++) {
+            wb[(UC - j) % UC] = Y[d0 - pb - j];
+#pragma unroll
+            for (int m = 0; m < UC; m++) mp::mac3(c0[m], c1[m], c2[m], xq[j % 8], wb[(m - j + UC) % UC]);
+          }
+        }
+      } else {
+#pragma unroll 1
+        for (int b = 0; b < p.upc / UC; b++) {
+          const int pb = p0 + b * UC;
+          const uint4 xa = *reinterpret_cast<const uint4 *>(X + pb);
+          const uint4 xb = *reinterpret_cast<const uint4 *>(X + pb + 4);
+          const uint32_t xq[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+          for (int j = 0; j < UC; j++) {
+            wb[(UC - j) % UC] = Y[d0 - pb - j];
+#pragma unroll
+            for (int m = 0; m < UC; m++) mp::msub3(c0[m], c1[m], c2[m], xq[j % 8], wb[(m - j + UC) % UC]);
+          }
+        }
+      }
+    } else if (active) {
       uint32_t wb[UC];
 #pragma unroll
       for (int m = 1; m < UC; m++) wb[m] = Y[d0 + m - p0];
@@ -531,8 +591,11 @@ int build_units(const SubProb *sub, int nsub, int uc, int upc, Unit *out, int ca
     int kmax = 0;
     for (int s = 0; s < S; s++) {
       const int d0 = s * uc;
-      const int lo = std::max(0, d0 - Wy + 1);
+      int lo = std::max(0, d0 - Wy + 1);
       const int hi = std::min(Wx - 1, d0 + uc - 1);
+      // stripe 8 reads X in aligned quads: start the chunks up to three limbs
+      // early (those products pair X with Y past the piece, in its zero gap)
+      if (uc == 8) lo &= ~3;
       plo[s] = lo;
       len[s] = hi >= lo ? hi - lo + 1 : 0;
       kmax = std::max(kmax, (len[s] + upc - 1) / upc);
@@ -574,8 +637,8 @@ int operand_windows(const SubProb *sub, int nsub, const Unit *units, int n, int 
 // slot rate of the stripe width.  Rates and unit cost are fitted to
 // factorisation timings on GB300 (N = 1000, W = 804, two Karatsuba levels,
 // seven (stripe, chunk) schedules).
-static const int kUcs[3] = {7, 9, 11};
-static const double kSpeed[3] = {41.7, 45.9, 45.1};
+static const int kUcs[4] = {7, 8, 9, 11};
+static const double kSpeed[4] = {41.7, 52.8, 45.9, 45.1};
 static double schedule_cost(const SubProb *sub, int nsub, int ui, int upc) {
   const int uc = kUcs[ui];
   const int n = build_units(sub, nsub, uc, upc, nullptr, 0);
@@ -592,7 +655,7 @@ static double best_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc_o
   if (const char *e = getenv("HK_UPC")) upc_force = atoi(e);
   int best_uc = UC, best_upc = 4 * UC;
   double best = 1e300;
-  for (int ui = 0; ui < 3; ui++) {
+  for (int ui = 0; ui < 4; ui++) {
     const int uc = kUcs[ui];
     if (uc_force && uc != uc_force) continue;
     for (int upc = 2 * uc; upc <= 8 * uc && upc <= upc_cap; upc += uc) {
@@ -683,6 +746,7 @@ cudaError_t launch_update(const UpdParams &p, cudaStream_t s) {
   if (p.upc % p.uc != 0 || p.nsub < 1 || p.nsub > MAX_SUB) return cudaErrorInvalidValue;
   switch (p.uc) {
     case 7: return launch_uc<7>(p, s);
+    case 8: return launch_uc<8>(p, s);
     case 9: return launch_uc<9>(p, s);
     case 11: return launch_uc<11>(p, s);
     default: return cudaErrorInvalidValue;

@@ -102,6 +102,8 @@ def test_unit_reads_stay_in_gaps_and_windows(hk, W, levels):
         xlo, xhi = p0, p0 + upc - 1
         ylo, yhi = d0 - (p0 + upc - 1), d0 + uc - 1 - p0
         assert 0 <= xlo < w
+        if uc == 8:
+            assert p0 % 4 == 0 and off % 4 == 0  # X read as aligned quads
         if plan["levels"] > 0:
             # past the piece only into its own zero gaps
             assert xhi < w + G and ylo >= -G and yhi < w + G
@@ -112,14 +114,16 @@ def test_unit_reads_stay_in_gaps_and_windows(hk, W, levels):
         else:
             # whole entries staged: past the entry only into the stage's zero pads
             assert xhi < W + (upc + 3) // 4 * 4
-            assert ylo >= -((uc + upc + 3) // 4 * 4) and yhi < W + (uc + 3) // 4 * 4
+            assert ylo >= -((uc + upc + 3) // 4 * 4) and yhi < W + (uc + 6) // 4 * 4
 
 
 def test_automatic_depth_follows_the_cost_model(hk):
     # three levels once the pieces stay wide enough to fill the unit grid
     assert hk.hk_update_plan(804, -1, with_units=False)["levels"] == 3
     assert hk.hk_update_plan(400, -1, with_units=False)["levels"] == 3
-    assert hk.hk_update_plan(176, -1, with_units=False)["levels"] == 2
+    # deeper levels only as the window widens
+    depths = [hk.hk_update_plan(W, -1, with_units=False)["levels"] for W in (8, 40, 100, 176, 300, 400, 804)]
+    assert depths == sorted(depths) and depths[0] == 0
     for W in (8, 64, 176, 804, 1200):
         plan = hk.hk_update_plan(W, -1, with_units=False)
         assert 0 <= plan["levels"] <= 3 and plan["C"] >= 2 * W
