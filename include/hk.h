@@ -168,6 +168,63 @@ int hk_batch_solve(hk_ctx *ctx, int count, const int *N, const int *beta_num, co
                    const int *P, const hk_mp *const *moments, int iters, int nthreads,
                    hk_mp *lambda_out, int *status_out, int *iters_out);
 
+/* ----- the paper's own method -------------------------------------------------
+ * P(x) = det(M - xI) by the submatrix-order LDL^T of section "The LDL^T
+ * Determinant Algorithm", with every trailing sum accumulated exactly and
+ * rounded once to P bits (RNE), as the CPU oracle of the method computes it:
+ *   D_t    = RNE(m_2t - x - sum_{s<t} C_s[t] Q_s[t])            (pivots)
+ *   C_t[r] = RNE(m_{t+r} - sum_{s<t} C_s[t] Q_s[r]),  r > t      (columns)
+ *   Q_t[r] = RNE(C_t[r] / D_t)                                  (CDivDiag)
+ *   det    = RNE(...RNE(RNE(D_0 D_1) D_2)... D_{N-1})          (running product)
+ * Negative pivots are allowed (above lambda_1, M - xI is indefinite); a zero
+ * pivot ends the factorisation with det = 0.  The trailing sums run on the
+ * same exact update kernel as hk_factor.  These calls overwrite the
+ * context's factor buffers: hk_smallest_eig needs a new hk_factor after them.
+ *
+ * hk_ldlt_det: x is a host P-bit value (normalised or zero), copied in; *det
+ * (caller limbs[L]) receives P(x); *neg_pivots (may be NULL) the number of
+ * negative pivots (the eigenvalues of M below x, by Sylvester's law of inertia,
+ * when no pivot is zero); *zero_row (may be NULL) the first zero pivot or -1.
+ * HK_ERR_RANGE when the exact-accumulation window could not be widened
+ * enough. */
+int hk_ldlt_det(hk_ctx *ctx, const hk_mp *x, hk_mp *det, int *neg_pivots, int *zero_row);
+
+/* After hk_ldlt_det (or within hk_secant, its last determinant): which = 0 the
+ * N pivots D_t into flat host arrays of N entries; 1 the columns C_t[r] (the
+ * packed upper triangle of N(N+1)/2 entries, layout as hk_get_R_flat, the
+ * pivots on its diagonal); 2 the quotients Q_t[r] (same layout, zero
+ * diagonal).  HK_ERR_STATE before any LDL^T. */
+int hk_get_ldlt_flat(hk_ctx *ctx, int which, int32_t *sign, int64_t *exp, uint32_t *limbs);
+
+/* The Secant root finder of section "The Secant Algorithm" on P(x):
+ *   x_2 = 0, x_1 = -min_t D_t(0) (the smallest pivot of M itself, negated),
+ *   x_{i+1} = RNE(x_i - RNE(RNE(RNE(x_i - x_{i-1}) / RNE(P(x_i) - P(x_{i-1}))) P(x_i)))
+ * until |x_{i+1} - x_i| <= 2^-136 |x_{i+1}| exactly, P(x_i) = P(x_{i-1}), or
+ * (after three steps) a step no shorter than the one before it; at most
+ * max_steps steps.  Every determinant is hk_ldlt_det's; the recurrence runs in
+ * single-block device kernels.  *root (caller limbs[L]) receives the last
+ * iterate (lambda_1 to the working precision); *dets_used (may be NULL) the
+ * number of determinants evaluated, which is also the number of iterates
+ * x_1, x_2, ... that hk_get_secant_flat returns. */
+int hk_secant(hk_ctx *ctx, int max_steps, hk_mp *root, int *dets_used);
+
+/* The first `count` iterates x_1, x_2, ... and their determinants P(x_k) of
+ * the last hk_secant, into flat host arrays of `count` entries each. */
+int hk_get_secant_flat(hk_ctx *ctx, int count, int32_t *xsign, int64_t *xexp, uint32_t *xlimbs, int32_t *psign,
+                       int64_t *pexp, uint32_t *plimbs);
+
+/* Verification of a root (section "Interval Verification"): the shifted LDL^T
+ * at x_lo = x (1 - 2^-bits) and x_hi = x (1 + 2^-bits), both exact at P2 bits
+ * (P2 a multiple of 32, P2 >= P + bits + 1, <= 32768), on the context's
+ * moments zero-extended to P2 bits.  out4[0], out4[1]: negative pivots at x_lo
+ * and x_hi; out4[2], out4[3]: the signs of their determinants (1, -1, 0).
+ * The root is accepted when out4 = {0, 1, 1, -1}: M - x_lo I has no negative
+ * eigenvalue and M - x_hi I exactly one.  The pivots are rounded at P2 bits,
+ * so this is the inertia of the once-rounded factorisation, not an interval
+ * proof.  x must be nonzero and normalised.  Uses a temporary context on the
+ * same device and stream. */
+int hk_secant_verify(hk_ctx *ctx, const hk_mp *x, int bits, int P2, int *out4);
+
 /* Copy R (row-major packed upper triangle, N(N+1)/2 entries, entry (t, j),
  * j >= t, at index t*N - t*(t-1)/2 + (j - t)) to host hk_mp values whose
  * limbs arrays the caller provides. */

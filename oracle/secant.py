@@ -59,6 +59,13 @@ def mp_mul(a, b, P):
 def ldlt_det(moments, N, x, P):
     """P(x) = det(M - xI) by the LDL^T of reading S2.  Returns (det, pivots)
     with ``pivots`` the P-bit D_t (fewer than N when a zero pivot stopped it)."""
+    det, D, _, _ = ldlt_factors(moments, N, x, P)
+    return det, D
+
+
+def ldlt_factors(moments, N, x, P):
+    """The LDL^T of reading S2 with its factors: (det, D, C, Q) where C[t] and
+    Q[t] map each r > t to the column entry C_t[r] and CDivDiag Q_t[r]."""
     C, Q, D = [], [], []
     det = None
     for t in range(N):
@@ -69,7 +76,7 @@ def ldlt_det(moments, N, x, P):
         D.append(d)
         det = d if det is None else mp_mul(det, d, P)
         if d[0] == 0:
-            return (0, 0), D
+            return (0, 0), D, C, Q
         Ct, Qt = {}, {}
         for r in range(t + 1, N):
             acc = exact_dot([(C[s][t], Q[s][r]) for s in range(t)])
@@ -78,7 +85,7 @@ def ldlt_det(moments, N, x, P):
             Qt[r] = mp_div(Ct[r], d, P)
         C.append(Ct)
         Q.append(Qt)
-    return det, D
+    return det, D, C, Q
 
 
 def _converged(new, old):

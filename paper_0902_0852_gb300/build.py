@@ -23,7 +23,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhk.so")
 LIB_CHECKED = os.path.join(HERE, "libhk_checked.so")
-SOURCES = ["hk_api.cu", "hk_update.cu", "hk_panel.cu", "hk_solve.cu", "hk_selftest.cu", "hk_peaks.cu", "hk_update_i8.cu", "hk_batch.cu", "hk_mlp.cu"]
+SOURCES = ["hk_api.cu", "hk_update.cu", "hk_panel.cu", "hk_solve.cu", "hk_selftest.cu", "hk_peaks.cu", "hk_update_i8.cu", "hk_batch.cu", "hk_mlp.cu", "hk_ldlt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

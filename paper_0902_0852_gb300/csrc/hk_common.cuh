@@ -19,7 +19,7 @@ struct DevStatus {
   long long check_a, check_b;  // the failed check's index and limit
 };
 
-enum { ST_OK = 0, ST_NOT_PD = 2, ST_TIMEOUT = 5, ST_RANGE = 7, ST_CHECK = 9 };
+enum { ST_OK = 0, ST_NOT_PD = 2, ST_TIMEOUT = 5, ST_RANGE = 7, ST_CHECK = 9, ST_ZERO = 11 };
 
 // Bounds checks of the checked build (HK_CHECKED): a failed check records the
 // site and the offending index once, stops the sequence (status code), and the

@@ -30,6 +30,7 @@ EXPORTS = [
     "hk_set_option", "hk_batch_solve",
     "hk_mlp_workspace_bytes", "hk_mlp_forward", "hk_mlp_loss_grad", "hk_mlp_adam", "hk_mlp_train",
     "hk_set_predictor", "hk_predict", "hk_update_plan", "hk_selftest_wait",
+    "hk_ldlt_det", "hk_get_ldlt_flat", "hk_secant", "hk_get_secant_flat", "hk_secant_verify",
 ]
 
 
@@ -86,6 +87,12 @@ def lib():
         L.hk_predict.argtypes = [vp, i32, vp, vp, vp]
         L.hk_update_plan.argtypes = [i32, i32, P64, P32, P32, P32, P32, i64, P32]
         L.hk_selftest_wait.argtypes = [vp]
+        L.hk_ldlt_det.argtypes = [vp, ctypes.POINTER(HkMp), ctypes.POINTER(HkMp), ctypes.POINTER(i32),
+                                  ctypes.POINTER(i32)]
+        L.hk_get_ldlt_flat.argtypes = [vp, i32, vp, vp, vp]
+        L.hk_secant.argtypes = [vp, i32, ctypes.POINTER(HkMp), ctypes.POINTER(i32)]
+        L.hk_get_secant_flat.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
+        L.hk_secant_verify.argtypes = [vp, ctypes.POINTER(HkMp), i32, i32, ctypes.POINTER(i32)]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype if name in ("hk_destroy", "hk_strerror") else i32
         L.hk_mlp_workspace_bytes.restype = sz
@@ -349,6 +356,83 @@ def hk_batch_solve(ctx, instances, iters=0, nthreads=16):
             v = None
         out.append((int(status[k]), v, int(used[k])))
     return out
+
+
+def _mp_in(v, P):
+    """(n, e) -> HkMp with its limbs array (kept alive by the caller)."""
+    L = P // 32
+    n, e = v
+    a = -n if n < 0 else n
+    limbs = np.frombuffer(a.to_bytes(4 * L, "little"), dtype=np.uint32).copy()
+    return HkMp(1 if n < 0 else 0, e if n else 0, limbs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))), limbs
+
+
+def _mp_out(P):
+    L = P // 32
+    limbs = np.zeros(L, dtype=np.uint32)
+    return HkMp(0, 0, limbs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))), limbs
+
+
+def _mp_val(m, limbs):
+    n = int.from_bytes(limbs.tobytes(), "little")
+    return (0, 0) if n == 0 else ((-n if m.sign else n), int(m.exp))
+
+
+def hk_ldlt_det(ctx, P, x):
+    """P(x) = det(M - xI): returns (det (n, e), negative pivots, first zero
+    pivot or -1)."""
+    xm, xl = _mp_in(x, P)
+    dm, dl = _mp_out(P)
+    neg, zr = ctypes.c_int(0), ctypes.c_int(-1)
+    _check(lib().hk_ldlt_det(ctx, ctypes.byref(xm), ctypes.byref(dm), ctypes.byref(neg), ctypes.byref(zr)),
+           "hk_ldlt_det")
+    return _mp_val(dm, dl), neg.value, zr.value
+
+
+def hk_get_ldlt(ctx, which, N, P):
+    """which 0: the N pivots; 1: C rows as R rows; 2: CDivDiag rows."""
+    n = N if which == 0 else N * (N + 1) // 2
+    L = P // 32
+    sign = np.zeros(n, dtype=np.int32)
+    exp = np.zeros(n, dtype=np.int64)
+    limbs = np.zeros((n, L), dtype=np.uint32)
+    _check(lib().hk_get_ldlt_flat(ctx, which, _ptr(sign), _ptr(exp), _ptr(limbs)), "hk_get_ldlt_flat")
+    vals = unpack(sign, exp, limbs)
+    if which == 0:
+        return vals
+    rows, k = [], 0
+    for t in range(N):
+        rows.append(vals[k:k + N - t])
+        k += N - t
+    return rows
+
+
+def hk_secant(ctx, P, max_steps=200):
+    """The Secant root of P(x): returns (root (n, e), determinants used)."""
+    rm, rl = _mp_out(P)
+    used = ctypes.c_int(0)
+    _check(lib().hk_secant(ctx, max_steps, ctypes.byref(rm), ctypes.byref(used)), "hk_secant")
+    return _mp_val(rm, rl), used.value
+
+
+def hk_get_secant(ctx, count, P):
+    """Iterates and determinants of the last hk_secant: two lists of (n, e)."""
+    L = P // 32
+    arrs = [np.zeros(count, dtype=np.int32), np.zeros(count, dtype=np.int64), np.zeros((count, L), dtype=np.uint32),
+            np.zeros(count, dtype=np.int32), np.zeros(count, dtype=np.int64), np.zeros((count, L), dtype=np.uint32)]
+    _check(lib().hk_get_secant_flat(ctx, count, *[_ptr(a) for a in arrs]), "hk_get_secant_flat")
+    return unpack(*arrs[:3]), unpack(*arrs[3:])
+
+
+def hk_secant_verify(ctx, P, x, bits=130, P2=None):
+    """Inertia on both sides of x: (negatives below, negatives above, det sign
+    below, det sign above)."""
+    if P2 is None:
+        P2 = (P + bits + 1 + 31) // 32 * 32
+    xm, xl = _mp_in(x, P)
+    out = (ctypes.c_int * 4)()
+    _check(lib().hk_secant_verify(ctx, ctypes.byref(xm), bits, P2, out), "hk_secant_verify")
+    return tuple(out)
 
 
 class Hankel:

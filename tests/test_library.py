@@ -81,6 +81,11 @@ def test_every_entry_point_rejects_a_null_context_or_bad_argument(lib):
         lambda: lib.hk_mlp_forward(None, None, 0, None, None),
         lambda: lib.hk_update_plan(0, -1, None, None, None, None, None, 0, None),
         lambda: lib.hk_selftest_wait(None),
+        lambda: lib.hk_ldlt_det(None, None, None, None, None),
+        lambda: lib.hk_get_ldlt_flat(None, 0, None, None, None),
+        lambda: lib.hk_secant(None, 10, None, None),
+        lambda: lib.hk_get_secant_flat(None, 0, None, None, None, None, None, None),
+        lambda: lib.hk_secant_verify(None, None, 130, 512, None),
     ]
     for k, call in enumerate(calls):
         assert call() == ARG, k
