@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-predicted", action="store_true",
                     help="skip the predicted-precision time-to-lambda comparison (after the timed region)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the after-region comparisons (Secant, INT8 update, batched sweep)")
     return ap.parse_args()
 
 
@@ -61,35 +63,30 @@ def step_macs(N, T):
 # CPU oracle sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
 
-ORACLE_ROWS = 8  # panel steps (rows of R) in the timed oracle sample
+ORACLE_STEPS = 16  # panel steps in the timed oracle sample
 
 
-def oracle_sample_setup(N, P, row0, last):
-    """Inputs of rows row0 .. last-1 of the beta = 1 factorisation: moments k!
-    and, for every column j >= row0, its entries in the rows above `last - 1`,
-    from the exact closed form i! C(i, k) (equal to the oracle's own rows at
-    this P), so that each sample row is computed from exact finished rows."""
-    from math import comb, factorial
+def oracle_sample_setup(N, P, steps):
+    """Inputs of the first `steps` panel steps of the beta = 1 factorisation:
+    rows t < steps of R from the exact closed form i! C(i, t) (equal to the
+    oracle's own rows at this P; oracle.cholesky_factorial)."""
     import oracle
-    from paper_0902_0852_gb300 import inputs
-    m = inputs.moments(N, (1, 1), P)
-    fact = [factorial(k) for k in range(N)]
-    col = {j: [oracle.rne(fact[j] * comb(j, t), 0, P) for t in range(last - 1)] for j in range(row0, N)}
-    return m, col
+    return oracle.cholesky_factorial(N, P, rows=steps)
 
 
 def _oracle_chunk(args):
-    """The oracle's own row routine on the sample rows for one share of the
-    columns; returns (worker pid, MACs, seconds spent in the oracle)."""
+    """The oracle's exact dot product on one share of the sample: for each
+    entry (i, j), i <= j, the contributions sum_{t < min(i, steps)} R_ti R_tj
+    of the first panel steps.  Returns (worker pid, MACs, seconds)."""
     import oracle
-    rows, m, colrows, cols, P = args
+    rows, cols, steps = args  # rows[t] = {j: R_tj}; cols = list of (i, j)
     t0 = time.perf_counter()
     macs = 0
-    for r in rows:
-        sub = {j: c[:r] for j, c in cols.items() if j >= r}
-        if sub:
-            oracle.cholesky_row(r, m, colrows[r], sub, P)
-            macs += r * len(sub)
+    for i, j in cols:
+        k = min(i, steps)
+        if k:
+            oracle.exact_dot([(rows[t][i], rows[t][j]) for t in range(k)])
+            macs += k
     return os.getpid(), macs, time.perf_counter() - t0
 
 
@@ -103,17 +100,28 @@ def make_pool(cores):
     return pool
 
 
-def oracle_sample(pool, cores, N, P, row0, last, setup):
-    """The oracle on panel steps (rows) row0 .. last-1 of the N x N
-    factorisation, all columns, split over `cores` processes.  Each worker
-    times only the oracle's arithmetic (its share of the inputs is shipped
-    before its clock starts); the sample's time is the busiest worker's total.
-    Returns (MACs, seconds)."""
-    m, col = setup
-    rows = list(range(row0, last))
-    colrows = {r: col[r][:r] for r in rows}
-    js = list(range(row0, N))
-    tasks = [(rows, m, colrows, {j: col[j] for j in js[k::cores]}, P) for k in range(cores) if js[k::cores]]
+def oracle_tasks(N, steps, setup, cores):
+    """The sample's entries split by column over `cores` workers, each shipped
+    only the rows' entries of its columns."""
+    Rrows = setup
+    tasks = []
+    for k in range(cores):
+        js = list(range(1 + k, N, cores))
+        if not js:
+            continue
+        need = set(js)
+        cols = [(i, j) for j in js for i in range(1, j + 1)]
+        need |= {i for i, _ in cols}
+        rows = [{c: Rrows[t][c - t] for c in need if c >= t} for t in range(len(Rrows))]
+        tasks.append((rows, cols, steps))
+    return tasks
+
+
+def oracle_sample(pool, tasks):
+    """The oracle on the first panel steps of the N x N factorisation, split
+    over the pool.  Each worker times only the oracle's arithmetic (its share
+    of the inputs is shipped before its clock starts); the sample's time is
+    the busiest worker's total.  Returns (MACs, seconds)."""
     busy, macs = {}, 0
     for pid, mc, sec in pool.map(_oracle_chunk, tasks):
         busy[pid] = busy.get(pid, 0.0) + sec
@@ -121,18 +129,16 @@ def oracle_sample(pool, cores, N, P, row0, last, setup):
     return macs, max(busy.values())
 
 
-def oracle_single_thread(N, P, row0, setup, ncols=64):
-    """The oracle on one core: row row0 for its first `ncols` columns, in this
-    process.  Returns (MACs, seconds)."""
-    m, col = setup
-    js = list(range(row0, min(N, row0 + ncols)))
-    _, macs, sec = _oracle_chunk(([row0], m, {row0: col[row0][:row0]}, {j: col[j] for j in js}, P))
+def oracle_single_thread(tasks, limit=64):
+    """The oracle on one core: the first `limit` entries of the first share,
+    in this process.  Returns (MACs, seconds)."""
+    rows, cols, steps = tasks[0]
+    _, macs, sec = _oracle_chunk((rows, cols[-limit:], steps))
     return macs, sec
 
 
-def sample_rows(N):
-    row0 = N // 2
-    return row0, min(N, row0 + ORACLE_ROWS)
+def sample_macs(N, steps):
+    return sum(min(i, steps) * (N - i) for i in range(1, N))
 
 
 def reduce_over_ranks(t_dev, t_e2e, macs, macs_e2e, device):
@@ -196,22 +202,22 @@ def run_reference(args):
     if rank != 0:
         return
     N, P = args.N, args.P
-    row0, last = sample_rows(N)
     cores = os.cpu_count() or 1
     pool = make_pool(cores)
-    setup = oracle_sample_setup(N, P, row0, last)
+    tasks = oracle_tasks(N, ORACLE_STEPS, oracle_sample_setup(N, P, ORACLE_STEPS), cores)
     for _ in range(args.warmup):
-        oracle_sample(pool, cores, N, P, row0, last, setup)
+        oracle_sample(pool, tasks)
     tot_m, tot_t = 0, 0.0
     for _ in range(args.steps):
-        m, t = oracle_sample(pool, cores, N, P, row0, last, setup)
+        m, t = oracle_sample(pool, tasks)
         tot_m += m
         tot_t += t
     pool.shutdown()
-    m1, t1 = oracle_single_thread(N, P, row0, setup)
+    m1, t1 = oracle_single_thread(tasks)
     v = tot_m / tot_t
-    sample = (f"{last - row0} panel steps (rows {row0}..{last - 1}) of the N={N}, P={P}, beta=1 factorisation, "
-              f"all columns ({tot_m // args.steps} MACs per step; time in the oracle, inputs shipped untimed)")
+    sample = (f"the first {ORACLE_STEPS} panel steps of the N={N}, P={P}, beta=1 factorisation: the exact "
+              f"contributions sum_(t<min(i,{ORACLE_STEPS})) R_ti R_tj to every entry ({tot_m // args.steps} MACs per "
+              f"step; time in the oracle, inputs shipped untimed)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
@@ -221,7 +227,7 @@ def run_reference(args):
                    "P": P, "beta": "1"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                          "single_thread": {"value": m1 / t1, "unit": UNIT,
-                                           "sample": f"row {row0}, first 64 columns ({m1} MACs, one process)"}},
+                                           "sample": f"64 entries of the same sample ({m1} MACs, one process)"}},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -245,18 +251,17 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        row0, last = sample_rows(N)
         pool = make_pool(cores)
-        setup = oracle_sample_setup(N, P, row0, last)
-        m_, t_ = oracle_sample(pool, cores, N, P, row0, last, setup)
+        tasks = oracle_tasks(N, ORACLE_STEPS, oracle_sample_setup(N, P, ORACLE_STEPS), cores)
+        m_, t_ = oracle_sample(pool, tasks)
         pool.shutdown()
-        m1, t1 = oracle_single_thread(N, P, row0, setup)
+        m1, t1 = oracle_single_thread(tasks)
         cpu = {"value": m_ / t_, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{last - row0} panel steps (rows {row0}..{last - 1}) of the N={N}, P={P}, beta=1 "
-                         f"factorisation, all columns ({m_} MACs, {t_:.1f} s in the oracle, inputs shipped "
-                         f"untimed)",
+               "sample": f"the first {ORACLE_STEPS} panel steps of the N={N}, P={P}, beta=1 factorisation: the "
+                         f"exact contributions of rows t < {ORACLE_STEPS} to every entry ({m_} MACs, {t_:.1f} s in "
+                         f"the oracle, inputs shipped untimed)",
                "single_thread": {"value": m1 / t1, "unit": UNIT,
-                                 "sample": f"row {row0}, first 64 columns ({m1} MACs, one process)"}}
+                                 "sample": f"64 entries of the same sample ({m1} MACs, one process)"}}
 
     import numpy as np
     import torch
@@ -375,15 +380,16 @@ def main():
         "factor_macs_per_s": (N - 1) * N * (N + 1) / 6 / (fac_ms / args.steps / 1e3),
         "limb_products_per_s_factor": limbprod / args.steps / (fac_ms / args.steps / 1e3),
         "e2e": {"value": macs_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlimbprod/s",
-                     "frac": achieved / peak, "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": executed, "peak": peak, "unit": "Tlimbprod/s",
+                     "frac": executed / peak, "traffic": traffic,
                      "kernel": "k_update (exact trailing update), factor launches",
                      "peak_basis": f"{n_sm} SMs x 64 IMAD/clk/SM x {max_mhz:.0f} MHz / 2 IMAD per 32x32->64 "
                                    f"limb product (probe: {peaks['imad_per_clk_sm']:.1f} IMAD/clk/SM)",
-                     "achieved_basis": f"algorithmic L^2 = {L * L} limb products per MAC (schoolbook count); the "
-                                       f"kernel executes {st['limbprod_per_mac']} per MAC ({st['karatsuba_levels']} "
-                                       f"Karatsuba levels on window W = {st['W']})",
-                     "executed": executed, "executed_frac": executed / peak},
+                     "achieved_basis": f"limb products the kernel executes: {st['limbprod_per_mac']} per P-bit MAC "
+                                       f"({st['karatsuba_levels']} Karatsuba levels on window W = {st['W']})",
+                     "algorithmic": achieved, "algorithmic_frac": achieved / peak,
+                     "algorithmic_basis": f"schoolbook L^2 = {L * L} limb products per MAC (the metric's unit); "
+                                          f"above 1 because Karatsuba executes fewer products"},
         "int_probe": peaks,
         "clocks": clocks,
         "gpu_launches": sum(r[3]["launches"] for r in recs),
@@ -391,10 +397,89 @@ def main():
     out["solve_window_limbs"] = {"max": st.get("solve_wv_max"), "mean": st.get("solve_wv_mean"), "W": st["W"]}
     if cpu is not None:
         out["cpu_baseline"] = cpu
+    if world == 1:
+        # the GPU on the oracle's sample: the first panel steps' update contributions
+        s_ms, s_macs = hk.hk_time_update_slice(h.ctx, ORACLE_STEPS)
+        out["gpu_oracle_slice"] = {"panel_steps": ORACLE_STEPS, "macs": s_macs, "ms": s_ms,
+                                   "value": s_macs / (s_ms / 1e3), "unit": UNIT,
+                                   "what": "the exact update kernel on the same sample as cpu_baseline"}
+    if world == 1 and not args.no_extras:
+        out["secant"] = secant_comparison(h, N, beta, P, lam, t_dev / args.steps)
     h.close()
+    if world == 1 and not args.no_extras:
+        out["int8_update"] = int8_comparison(N, beta, P, moments, peaks, clocks)
+        out["batched_sweep"] = batched_sweep()
     if not args.no_predicted and world == 1:
         out["time_to_lambda_predicted"] = predicted_comparison(N, beta)
     print(json.dumps(out))
+
+
+def secant_comparison(h, N, beta, P, lam_ii, t_ii):
+    """The paper's own route to lambda_1 on the same instance: the Secant
+    recurrence on det(M - xI) (one shifted LDL^T per iterate), then the
+    inertia on both sides of the root at P + 160 bits; timed around the
+    library calls after the benchmark's timed region."""
+    from paper_0902_0852_gb300 import hk
+    from paper_0902_0852_gb300.predictor import rel_err_bits
+    t0 = time.perf_counter()
+    root, dets = hk.hk_secant(h.ctx, P)
+    t1 = time.perf_counter()
+    out4 = hk.hk_secant_verify(h.ctx, P, root, 130)
+    t2 = time.perf_counter()
+    agree = rel_err_bits(root, lam_ii)
+    return {"t_secant_s": round(t1 - t0, 3), "determinants": dets, "t_verify_s": round(t2 - t1, 3),
+            "verified": list(out4) == [0, 1, 1, -1], "inertia": list(out4),
+            "t_inverse_iteration_step_s": round(t_ii, 3),
+            "agree_bits_with_inverse_iteration": None if agree is None else min(agree, 1e9),
+            "speedup_of_inverse_iteration": round((t1 - t0) / t_ii, 3)}
+
+
+def int8_comparison(N, beta, P, moments, peaks, clocks):
+    """The INT8 tensor form of the factor update (mma.sync m16n8k32 u8) on the
+    same instance, once, after the timed region: its update time, u8 multiply-
+    adds per second over the plain entries (16 W^2 per P-bit MAC), the fraction
+    of the measured mma.sync u8 rate, and R equal to the IMAD path's."""
+    import torch
+    from paper_0902_0852_gb300 import hk
+    with hk.Hankel(0) as h:
+        h.load(N, beta, P, moments)
+        h.factor()
+        ref = hk.hk_get_R_flat(h.ctx, N, P)
+        ms_imad = h.timings()["update_ms"]
+        h.set_update_path(1)
+        h.factor()
+        tm = h.timings()
+        st = h.stats()
+        got = hk.hk_get_R_flat(h.ctx, N, P)
+    same = all(bool((a == b).all()) for a, b in zip(ref, got))
+    W = st["W"]
+    u8 = (N - 1) * N * (N + 1) / 6 * 16 * W * W
+    rate = u8 / (tm["update_ms"] / 1e3)
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = peaks["mma_u8_mac_per_clk_sm"] * n_sm * mhz * 1e6
+    return {"update_ms": round(tm["update_ms"], 1), "update_ms_imad": round(ms_imad, 1), "u8_mac_per_s": rate,
+            "peak_u8_mac_per_s": peak, "frac_of_mma_u8_peak": rate / peak, "R_bit_identical_to_imad": same,
+            "peak_basis": f"probe {peaks['mma_u8_mac_per_clk_sm']:.1f} u8 MAC/clk/SM x {n_sm} SMs x {mhz:.0f} MHz",
+            "work_basis": f"16 W^2 u8 MACs per P-bit MAC over plain entries, W = {W}"}
+
+
+def batched_sweep():
+    """The batched sweep: 64 instances (seed 0), N in [100, 600], beta in
+    {3/4, 1, 3/2, 2, 3}, P by the sweep's rule, solved to convergence through
+    hk_batch_solve (host worker pool of contexts on concurrent streams),
+    escalating P by 1024 on a failed pivot; timed around the library calls."""
+    from paper_0902_0852_gb300 import batch, inputs
+    inst = inputs.batched_instances(64, 0)
+    t0 = time.perf_counter()
+    res = batch.solve_batch(inst)
+    dt = time.perf_counter() - t0
+    return {"instances": len(inst), "seconds": round(dt, 3),
+            "escalations": sum(r["escalations"] for r in res),
+            "iterations": sum(abs(r["iters"]) for r in res),
+            "all_ok": all(r["status"] == 0 for r in res),
+            "macs": sum((r["N"] - 1) * r["N"] * (r["N"] + 1) // 6 for r in res),
+            "scheduler": "host worker pool (16 contexts on non-blocking streams, largest first)"}
 
 
 def predicted_comparison(N, beta):

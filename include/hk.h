@@ -135,9 +135,16 @@ int hk_set_update_path(hk_ctx *ctx, int path);
  *                           6e10 (default 2e9); a wait that runs out makes its
  *                           kernel record the timeout and return, and the call
  *                           returns HK_ERR_TIMEOUT; keeps the factorisation
- * None of the first five changes any result: every sum is exact. */
+ *   HK_OPT_LOOKAHEAD        1 (default): while block b's rows are finished one
+ *                           by one (the sequential panel chain, on a high-
+ *                           priority stream), the update of block b + 1 by all
+ *                           rows up to block b - 1 runs on a low-priority
+ *                           stream, and only the contribution of block b waits
+ *                           for its panel; 0: one stream, strictly in order
+ * None of the first five, nor the lookahead, changes any result: every sum is
+ * exact. */
 enum { HK_OPT_UPDATE_PATH = 0, HK_OPT_KARATSUBA = 1, HK_OPT_GRAPH = 2, HK_OPT_AUTOTUNE = 3, HK_OPT_PANEL_ROWS = 4,
-       HK_OPT_MAX_ITERS = 5, HK_OPT_WAIT_NS = 6 };
+       HK_OPT_MAX_ITERS = 5, HK_OPT_WAIT_NS = 6, HK_OPT_LOOKAHEAD = 7 };
 int hk_set_option(hk_ctx *ctx, int option, long long value);
 
 /* Failure-detection self-test (no counterpart in the paper): on the context's
@@ -273,6 +280,16 @@ int hk_get_stats(hk_ctx *ctx, int64_t *out, int n);
  * non-blocking stream (events and copies ordered on it), so it neither waits
  * for nor blocks other streams, and several host threads may call it. */
 int hk_probe_int_peaks(int device, double *out, int n);
+
+/* Measurement hook (no counterpart in the paper): after hk_factor, re-runs the
+ * exact update kernel for the contributions of the first `tsteps` panel steps
+ * (rows t < tsteps of R) to every later entry -- sum_{t < min(i, tsteps)}
+ * R_ti R_tj for all i <= j -- into scratch column sums that are discarded,
+ * and returns the device time of those launches (*ms, CUDA events on the
+ * context's stream) and their P-bit multiply-accumulates (*macs).  The factor
+ * is not changed.  This is the slice of the factorisation that the CPU
+ * oracle's timed sample computes. */
+int hk_time_update_slice(hk_ctx *ctx, int tsteps, double *ms, double *macs);
 
 /* ----- self-test hooks of the device multiprecision library ----------------
  * Run one single-CTA device operation on host operands (copied in and out) so

@@ -197,7 +197,7 @@ def cholesky(moments, N, P, rows=None, workers=1):
     return R
 
 
-def cholesky_factorial(N, P):
+def cholesky_factorial(N, P, rows=None):
     """R of the beta = 1 matrix (m_k = k!, the paper's first N = 4 example)
     when P is wide enough for every step of ``cholesky`` to be exact.
 
@@ -208,7 +208,8 @@ def cholesky_factorial(N, P):
     quotient and every rounding of reading 1 are exact and ``cholesky``
     returns exactly these values.  This is that result written out (it needs
     no O(N^3) arithmetic); P too small for exactness raises ValueError.
-    Same layout as ``cholesky``: ``R[t][j - t] = R_tj``.
+    Same layout as ``cholesky``: ``R[t][j - t] = R_tj``; ``rows`` limits it to
+    the first rows (all columns).
     """
     f = 1
     for k in range(2, 2 * N - 1):
@@ -219,7 +220,7 @@ def cholesky_factorial(N, P):
     for k in range(1, N):
         fact[k] = fact[k - 1] * k
     R = []
-    for t in range(N):
+    for t in range(N if rows is None else min(rows, N)):
         row = []
         c = 1  # C(j, t) at j = t
         for j in range(t, N):

@@ -136,6 +136,12 @@ struct hk_ctx {
   long long top_margin = 0;  // extra bits above the a priori column bounds
   bool timing = true;
   // shifted LDL^T of M - xI (the paper's determinant), Secant and verification
+  // lookahead: the far part of the next block's update (rows two blocks back and
+  // earlier) runs on a low-priority stream while the current block's
+  // sequential panel chain runs on a high-priority one
+  bool lookahead = true;
+  cudaStream_t la_hi = nullptr, la_lo = nullptr;
+  std::vector<cudaEvent_t> la_ev;
   bool ldl_mode = false;     // the factor driver runs the LDL^T instead of Cholesky
   Arena ldl_arena, ldl_small;
   MpArr Qf{};                // CDivDiag in floating form
@@ -236,7 +242,11 @@ cudaError_t alloc_mp(hk_ctx *c, Arena &a, MpArr *m, size_t count, int L) {
 int round4(long long x) { return (int)((x + 3) / 4 * 4); }
 
 // --- event timing ---------------------------------------------------------------
-void ev_begin(hk_ctx *c, int kind) {
+void ev_begin(hk_ctx *c, int kind, cudaStream_t s);
+void ev_end(hk_ctx *c, cudaStream_t s);
+void ev_begin(hk_ctx *c, int kind) { ev_begin(c, kind, c->stream); }
+void ev_end(hk_ctx *c) { ev_end(c, c->stream); }
+void ev_begin(hk_ctx *c, int kind, cudaStream_t s) {
   if (!c->timing) return;
   if (c->evused == c->evpool.size()) {
     EvPair p;
@@ -250,11 +260,11 @@ void ev_begin(hk_ctx *c, int kind) {
   }
   if (c->evkind.size() < c->evpool.size()) c->evkind.resize(c->evpool.size());
   c->evkind[c->evused] = kind;
-  cudaEventRecord(c->evpool[c->evused].a, c->stream);
+  cudaEventRecord(c->evpool[c->evused].a, s);
 }
-void ev_end(hk_ctx *c) {
+void ev_end(hk_ctx *c, cudaStream_t s) {
   if (!c->timing || c->evused >= c->evpool.size()) return;
-  cudaEventRecord(c->evpool[c->evused].b, c->stream);
+  cudaEventRecord(c->evpool[c->evused].b, s);
   c->evused++;
 }
 void ev_collect(hk_ctx *c) {
@@ -570,7 +580,7 @@ int factor_attempt(hk_ctx *c, int r_start) {
     c->fac_arena.release();
     c->fac_N = c->fac_L = c->fac_W = 0;
     CK(alloc(c, c->fac_arena, &c->A, NT * (size_t)W));
-    CK(alloc(c, c->fac_arena, &c->colsum, (size_t)maxout * c->C));
+    CK(alloc(c, c->fac_arena, &c->colsum, 2 * (size_t)maxout * c->C));  // two blocks in flight
     c->Aexp = nullptr;
     if (levels > 0) CK(alloc(c, c->fac_arena, &c->Aexp, NT * (size_t)c->kl.stride));
     c->A_len = (long long)NT * W;
@@ -707,40 +717,98 @@ int factor_enqueue(hk_ctx *c, const Sched &sc, int r_start) {
     DBG(c, "realign", r_start, W);
     c->launches++;
   }
-  for (int r0 = r_start; r0 < N; r0 += nb) {
+  // streams: the panel chain (and the near update) on sP, the far updates on
+  // sU; without lookahead both are the context's stream
+  cudaStream_t sP = c->stream, sU = c->stream;
+  const int nblk = (N - r_start + nb - 1) / nb;
+  const bool la = c->lookahead && nblk > 2;
+  if (la) {
+    if (!c->la_hi) {
+      int lo = 0, hi = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      CK(cudaStreamCreateWithPriority(&c->la_hi, cudaStreamNonBlocking, hi));
+      CK(cudaStreamCreateWithPriority(&c->la_lo, cudaStreamNonBlocking, lo));
+    }
+    const size_t need = 3 * (size_t)nblk + 3;
+    while (c->la_ev.size() < need) {
+      cudaEvent_t e;
+      CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      c->la_ev.push_back(e);
+    }
+    // fork from the context's stream (and its realignment, if any)
+    CK(cudaEventRecord(c->la_ev[0], c->stream));
+    CK(cudaStreamWaitEvent(c->la_hi, c->la_ev[0], 0));
+    CK(cudaStreamWaitEvent(c->la_lo, c->la_ev[0], 0));
+    sP = c->la_hi;
+    sU = c->la_lo;
+  }
+  auto ev_panel = [&](int b) { return c->la_ev[3 + 3 * b]; };
+  auto ev_zero = [&](int b) { return c->la_ev[3 + 3 * b + 1]; };
+  auto ev_far = [&](int b) { return c->la_ev[3 + 3 * b + 2]; };
+  const size_t cs_block = (size_t)rows_outputs(N, 0, std::min(nb, N)) * c->C;
+  for (int b = 0, r0 = r_start; r0 < N; b++, r0 += nb) {
     const int r1 = std::min(N, r0 + nb);
     const long long nout = rows_outputs(N, r0, r1);
-    CK(cudaMemsetAsync(c->colsum, 0, sizeof(long long) * nout * c->C, c->stream));
+    long long *cs = c->colsum + (b % 2) * cs_block;
+    pp.colsum = cs;
+    up.colsum = cs;
+    lq.pp.colsum = cs;
     pp.r0 = r0;
     up.r0 = r0;
-    if (r0 > 0) {
+    // far update on sU: rows t < r0 - nb, final once block b - 2 is done (or
+    // before the first block when resuming); it shares the column sums with
+    // the near update below
+    if (la && b >= 2) CK(cudaStreamWaitEvent(sU, ev_panel(b - 2), 0));
+    CK(cudaMemsetAsync(cs, 0, sizeof(long long) * nout * c->C, sU));
+    if (la) CK(cudaEventRecord(ev_zero(b), sU));
+    const int tfar = la ? std::max(0, r0 - nb) : r0;
+    if (tfar > 0) {
       up.ra = r0;
       up.rb = r1;
       up.nout = (int)nout;
       up.t0 = 0;
-      up.t1 = r0;
-      up.tchunk = pick_tchunk(r0, cta_per_out * nout, target);
-      ev_begin(c, 0);
-      CK((c->update_path == 1 && !c->ldl_mode) ? launch_update_i8(up, c->stream) : launch_update(up, c->stream));
+      up.t1 = tfar;
+      up.tchunk = pick_tchunk(tfar, cta_per_out * nout, target);
+      ev_begin(c, 0, sU);
+      CK((c->update_path == 1 && !c->ldl_mode) ? launch_update_i8(up, sU) : launch_update(up, sU));
       DBG(c, "factor update", up.ra, up.t1);
-      ev_end(c);
+      ev_end(c, sU);
       c->launches++;
     }
+    if (la) {
+      CK(cudaEventRecord(ev_far(b), sU));
+      // near update on sP: the previous block's rows (after its panel chain)
+      CK(cudaStreamWaitEvent(sP, ev_zero(b), 0));
+      if (r0 > tfar) {
+        up.ra = r0;
+        up.rb = r1;
+        up.nout = (int)nout;
+        up.t0 = tfar;
+        up.t1 = r0;
+        up.tchunk = pick_tchunk(r0 - tfar, cta_per_out * nout, target);
+        ev_begin(c, 0, sP);
+        CK((c->update_path == 1 && !c->ldl_mode) ? launch_update_i8(up, sP) : launch_update(up, sP));
+        DBG(c, "factor update", up.ra, up.t1);
+        ev_end(c, sP);
+        c->launches++;
+      }
+      CK(cudaStreamWaitEvent(sP, ev_far(b), 0));
+    }
     for (int i = r0; i < r1; i++) {
-      ev_begin(c, 1);
+      ev_begin(c, 1, sP);
       if (c->ldl_mode) {
         lq.pp.r0 = r0;
-        CK(launch_ldl_pivot(lq, i, c->stream));
+        CK(launch_ldl_pivot(lq, i, sP));
         DBG(c, "ldl pivot", i, 0);
-        CK(launch_ldl_row(lq, i, c->stream));
+        CK(launch_ldl_row(lq, i, sP));
         DBG(c, "ldl row", i, 0);
       } else {
-        CK(launch_diag(pp, i, c->stream));
+        CK(launch_diag(pp, i, sP));
         DBG(c, "diag", i, 0);
-        CK(launch_offdiag(pp, i, c->stream));
+        CK(launch_offdiag(pp, i, sP));
         DBG(c, "offdiag", i, 0);
       }
-      ev_end(c);
+      ev_end(c, sP);
       c->launches += (i + 1 < N) ? 2 : 1;
       if (i + 1 < r1) {
         up.ra = i + 1;
@@ -749,13 +817,21 @@ int factor_enqueue(hk_ctx *c, const Sched &sc, int r_start) {
         up.t0 = i;
         up.t1 = i + 1;
         up.tchunk = 1;
-        ev_begin(c, 0);
-        CK((c->update_path == 1 && !c->ldl_mode) ? launch_update_i8(up, c->stream) : launch_update(up, c->stream));
+        ev_begin(c, 0, sP);
+        CK((c->update_path == 1 && !c->ldl_mode) ? launch_update_i8(up, sP) : launch_update(up, sP));
         DBG(c, "factor update", up.ra, up.t1);
-        ev_end(c);
+        ev_end(c, sP);
         c->launches++;
       }
     }
+    if (la) CK(cudaEventRecord(ev_panel(b), sP));
+  }
+  if (la) {
+    // join both streams back into the context's stream
+    CK(cudaEventRecord(c->la_ev[1], sU));
+    CK(cudaEventRecord(c->la_ev[2], sP));
+    CK(cudaStreamWaitEvent(c->stream, c->la_ev[1], 0));
+    CK(cudaStreamWaitEvent(c->stream, c->la_ev[2], 0));
   }
   return HK_OK;
 }
@@ -1160,6 +1236,9 @@ void hk_destroy(hk_ctx *c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->la_hi) cudaStreamDestroy(c->la_hi);
+  if (c->la_lo) cudaStreamDestroy(c->la_lo);
+  for (cudaEvent_t e : c->la_ev) cudaEventDestroy(e);
   c->sol_arena.release();
   c->fac_arena.release();
   c->res_arena.release();
@@ -1333,6 +1412,7 @@ static int factor_run(hk_ctx *c, int *bad_row) {
   // the LDL^T operands are the Cholesky factor's within a factor of two
   c->top_margin = c->ldl_mode ? 2 : 0;
   if (const char *e = getenv("HK_NB")) c->nb = std::max(1, atoi(e));  // panel block rows (tuning)
+  if (const char *e = getenv("HK_LOOKAHEAD")) c->lookahead = atoi(e) != 0;  // (tuning)
   if (const char *e = getenv("HK_KARATSUBA")) c->kar_levels = std::min(MAX_KAR, std::max(-1, atoi(e)));  // (tuning)
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -1448,6 +1528,9 @@ int hk_set_option(hk_ctx *c, int option, long long value) {
     case 6:  // limit of each bounded device wait, ns (R stays valid)
       if (value < 1000 || value > 60000000000LL) return HK_ERR_ARG;
       c->wait_ns = value;
+      return HK_OK;
+    case 7:  // lookahead: far updates overlap the panel chain on a second stream
+      c->lookahead = value != 0;
       return HK_OK;
     default:
       return HK_ERR_ARG;
@@ -1961,6 +2044,73 @@ int hk_secant_verify(hk_ctx *c, const hk_mp *x, int bits, int P2, int *out4) {
   tmp.release();
   hk_destroy(c2);
   return rc;
+}
+
+
+int hk_time_update_slice(hk_ctx *c, int tsteps, double *ms, double *macs) {
+  if (!c || tsteps < 1 || !ms || !macs) return HK_ERR_ARG;
+  if (!c->factored) return HK_ERR_STATE;
+  cudaSetDevice(c->device);
+  const int N = c->N, nb = c->nb, W = c->W;
+  const int ts = std::min(tsteps, N);
+  const int levels = c->fac_levels;
+  Sched sc;
+  CK(sched_for(c, W, W, levels, &sc));
+  UpdParams up;
+  std::memset(&up, 0, sizeof(up));
+  up.wait_ns = c->wait_ns;
+  up.mode = M_FACTOR;
+  up.N = N;
+  up.A = levels > 0 ? c->Aexp : c->A;
+  up.Asign = c->Asign;
+  up.astride = levels > 0 ? c->kl.stride : W;
+  up.cx = up.cy = up.astride;
+  up.colsum = c->colsum;
+  up.a_len = levels > 0 ? c->Aexp_len : c->A_len;
+  up.colsum_len = c->colsum_len;
+  fill_sched(up, sc);
+  up.st = c->st;
+  const long long cta_per_out = (sc.n + UNT - 1) / UNT;
+  const long long target = 6LL * sm_count(c) * 3;
+  CK(reset_status(c));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, c->stream));
+  long long m = 0;
+  // the contributions of the first `ts` rows (panel steps) to every later
+  // entry: rows i < ts take t < i, later rows all t < ts; the result goes to
+  // the factor's column-sum scratch and is discarded
+  for (int r0 = 0; r0 < N; r0 += nb) {
+    const int r1 = std::min(N, r0 + nb);
+    for (int i = r0; i < r1;) {
+      const bool early = i < ts;
+      const int ra = i, rb = early ? i + 1 : r1;
+      const int tend = early ? i : ts;
+      i = rb;
+      if (tend <= 0) continue;
+      up.r0 = r0;
+      up.ra = ra;
+      up.rb = rb;
+      up.nout = (int)rows_outputs(N, ra, rb);
+      up.t0 = 0;
+      up.t1 = tend;
+      up.tchunk = pick_tchunk(tend, cta_per_out * up.nout, target);
+      CK(launch_update(up, c->stream));
+      m += (long long)tend * up.nout;
+    }
+  }
+  CK(cudaEventRecord(e1, c->stream));
+  CK(cudaEventSynchronize(e1));
+  float t = 0;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const DevStatus st = read_status(c);
+  if (st.timeout) return HK_ERR_TIMEOUT;
+  *ms = t;
+  *macs = (double)m;
+  return HK_OK;
 }
 
 }  // extern "C"

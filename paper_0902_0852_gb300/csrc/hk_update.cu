@@ -331,6 +331,8 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
     const int neg = sneg[s];
     if (UC == 8 && active) {
       // X read as aligned quads: two 128-bit shared loads per eight p-steps
+      // (the window below stays scalar: quads at the stripes' stride of eight
+      // limbs measured slower)
       uint32_t wb[UC];
 #pragma unroll
       for (int m = 1; m < UC; m++) wb[m] = Y[d0 + m - p0];

@@ -31,6 +31,7 @@ EXPORTS = [
     "hk_mlp_workspace_bytes", "hk_mlp_forward", "hk_mlp_loss_grad", "hk_mlp_adam", "hk_mlp_train",
     "hk_set_predictor", "hk_predict", "hk_update_plan", "hk_selftest_wait",
     "hk_ldlt_det", "hk_get_ldlt_flat", "hk_secant", "hk_get_secant_flat", "hk_secant_verify",
+    "hk_time_update_slice",
 ]
 
 
@@ -93,6 +94,7 @@ def lib():
         L.hk_secant.argtypes = [vp, i32, ctypes.POINTER(HkMp), ctypes.POINTER(i32)]
         L.hk_get_secant_flat.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
         L.hk_secant_verify.argtypes = [vp, ctypes.POINTER(HkMp), i32, i32, ctypes.POINTER(i32)]
+        L.hk_time_update_slice.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype if name in ("hk_destroy", "hk_strerror") else i32
         L.hk_mlp_workspace_bytes.restype = sz
@@ -306,7 +308,7 @@ def hk_mp_op_noalloc(op, L, x, ex, y, ey, out, eo, stream=None):
 
 
 (HK_OPT_UPDATE_PATH, HK_OPT_KARATSUBA, HK_OPT_GRAPH, HK_OPT_AUTOTUNE, HK_OPT_PANEL_ROWS, HK_OPT_MAX_ITERS,
- HK_OPT_WAIT_NS) = range(7)
+ HK_OPT_WAIT_NS, HK_OPT_LOOKAHEAD) = range(8)
 
 
 def hk_set_option(ctx, option, value):
@@ -376,6 +378,13 @@ def _mp_out(P):
 def _mp_val(m, limbs):
     n = int.from_bytes(limbs.tobytes(), "little")
     return (0, 0) if n == 0 else ((-n if m.sign else n), int(m.exp))
+
+
+def hk_time_update_slice(ctx, tsteps):
+    """(device ms, MACs) of the update contributions of the first tsteps rows."""
+    ms, macs = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib().hk_time_update_slice(ctx, tsteps, ctypes.byref(ms), ctypes.byref(macs)), "hk_time_update_slice")
+    return ms.value, macs.value
 
 
 def hk_ldlt_det(ctx, P, x):

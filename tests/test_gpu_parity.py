@@ -231,6 +231,29 @@ def test_karatsuba_depths_bit_identical(hk, N, beta, P):
     assert len(seen) == 4
 
 
+@pytest.mark.parametrize("N,beta,P,nb", [(100, (7, 4), 1024, 16), (90, (1, 1), 768, 8), (64, (3, 4), 2048, 16)])
+def test_lookahead_bit_identical(hk, N, beta, P, nb):
+    """The lookahead (far updates of the next block on a low-priority stream
+    while the panel chain runs on a high-priority one, two column-sum buffers
+    in flight) reorders only exact integer additions: R and the history equal
+    the oracle's with it on or off, with graph capture on or off."""
+    m = inputs.moments(N, beta, P)
+    Ro = oracle.cholesky(m, N, P)
+    _, hist_o, _ = oracle.inverse_iteration(Ro, P, 3)
+    for la, graph in ((1, 0), (0, 0), (1, 1)):
+        with hk.Hankel(0) as h:
+            h.set_option(hk.HK_OPT_LOOKAHEAD, la)
+            h.set_option(hk.HK_OPT_GRAPH, graph)
+            h.set_option(hk.HK_OPT_PANEL_ROWS, nb)
+            h.load(N, beta, P, m)
+            h.factor()
+            R = h.R()
+            lam, used = h.smallest_eig(3)
+            hist = h.history(3)
+        assert R == Ro, (la, graph)
+        assert hist == hist_o, (la, graph)
+
+
 # Slack 0 fails in the first block (a restart).  L = P/32 = 15 leaves exactly
 # one limb (32 bits) of slack after W is rounded up to a multiple of 4; for
 # beta = 3 and 4 the first row's entries spread less than that (at most 18 and
