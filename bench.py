@@ -33,7 +33,7 @@ SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.act
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 # DRAM bytes (read + write) per executed limb product of the update kernel, from
 # one ncu capture of the current kernel version; None when not measured.
-UPDATE_TRAFFIC_BYTES_PER_LIMBPROD = (18.6326e9 + 0.0326e9) / (3976 * 256 * 265833)  # k_update_karatsuba3_N512_P24576_full.md
+UPDATE_TRAFFIC_BYTES_PER_LIMBPROD = None  # the update kernel changed since the last DRAM capture
 
 
 def parse():
@@ -301,8 +301,18 @@ def main():
         lam, used = h.smallest_eig(args.iters)
         return lam, used, h.timings(), h.stats()
 
-    for _ in range(args.warmup):
-        step(True)
+    # warm-up; the last warm-up step runs with the lookahead off, so that its
+    # per-launch events time the update kernels alone (the roofline below);
+    # the timed steps overlap the panel chain with the updates
+    serial = None
+    for k in range(args.warmup):
+        last = k == args.warmup - 1
+        if last:
+            h.set_option(hk.HK_OPT_LOOKAHEAD, 0)
+        r = step(True)
+        if last:
+            serial = r
+            h.set_option(hk.HK_OPT_LOOKAHEAD, 1)
     torch.cuda.synchronize()
 
     # ---- timed: device-resident inputs ----
@@ -340,14 +350,16 @@ def main():
         h.close()
         return
 
-    # roofline of the update kernel (factor launches), CUDA events per launch
-    upd_ms = sum(r[2]["update_ms"] for r in recs)
+    # roofline of the update kernel (factor launches), CUDA events per launch,
+    # from the warm-up step without the lookahead (kernels timed alone)
+    ref = serial if serial is not None else recs[-1]
+    upd_ms = ref[2]["update_ms"]
     fac_ms = sum(r[2]["factor_ms"] for r in recs)
     eig_ms = sum(r[2]["eig_ms"] for r in recs)
-    limbprod = (N - 1) * N * (N + 1) // 6 * L * L * args.steps
+    limbprod = (N - 1) * N * (N + 1) // 6 * L * L
     achieved = limbprod / (upd_ms / 1e3) / 1e12
-    st = recs[-1][3]
-    executed = (N - 1) * N * (N + 1) // 6 * st["limbprod_per_mac"] * args.steps / (upd_ms / 1e3) / 1e12
+    st = ref[3]
+    executed = (N - 1) * N * (N + 1) // 6 * st["limbprod_per_mac"] / (upd_ms / 1e3) / 1e12
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     peak = n_sm * 64 * max_mhz * 1e6 / 2 / 1e12
@@ -375,10 +387,13 @@ def main():
         "lambda_min_table3": "1.0892e-52" if (N, P) == (1000, 24576) else None,
         "factor_ms": fac_ms / args.steps, "inverse_iteration_ms": eig_ms / args.steps,
         # per-phase device time (CUDA events around each launch group): update
-        # kernels of the factor, its diagonal/row kernels, and the solves
+        # kernels of the factor, its diagonal/row kernels, and the solves; the
+        # timed steps overlap the first two (lookahead), the warm-up step
+        # without lookahead times them alone
         "phases_ms": {k: sum(r[2][k] for r in recs) / args.steps for k in ("update_ms", "panel_ms", "solve_ms")},
+        "phases_ms_serial": {k: ref[2][k] for k in ("update_ms", "panel_ms", "solve_ms", "factor_ms")},
         "factor_macs_per_s": (N - 1) * N * (N + 1) / 6 / (fac_ms / args.steps / 1e3),
-        "limb_products_per_s_factor": limbprod / args.steps / (fac_ms / args.steps / 1e3),
+        "limb_products_per_s_factor": limbprod / (fac_ms / args.steps / 1e3),
         "e2e": {"value": macs_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": executed, "peak": peak, "unit": "Tlimbprod/s",
                      "frac": executed / peak, "traffic": traffic,

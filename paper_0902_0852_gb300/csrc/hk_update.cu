@@ -292,7 +292,11 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
   bool active = u < p.nunits;
   const Unit un = active ? p.units[u] : Unit{0, 0};
   const int sp = (un.d0 >> 24) & 0xff;
-  const int d0 = un.d0 & 0xffffff, p0 = un.p0;
+  const int d0 = un.d0 & 0xffffff;
+  // stripe 8: chunk start in bits 0..15, its length in groups of eight p-steps
+  // in bits 16..23; other stripes: chunks of p.upc
+  const int p0 = UC == 8 ? (un.p0 & 0xffff) : un.p0;
+  const int ngrp = UC == 8 ? ((un.p0 >> 16) & 0xff) : p.upc / UC;
   // a unit table entry must name one of this launch's sub-problems (always
   // checked: a bad entry would index the operand tiles with wrong offsets)
   if (active && sp >= p.nsub) active = check_fail(p.st, 5, sp, p.nsub);
@@ -306,8 +310,8 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
     // (inside the block's operand window when it has one)
     const long long xlim = p.nxb ? p.xlen[blockIdx.x] : Xsz;
     const long long ymin = p.nxb ? YPADL : 0, ylim = p.nxb ? YPADL + p.xlen[blockIdx.x] : Ysz;
-    const long long xlo = xoff + p0, xhi = xoff + p0 + p.upc - 1;
-    const long long ylo = YPADL + yoff + d0 - p0 - p.upc + 1, yhi = YPADL + yoff + d0 - p0 + UC - 1;
+    const long long xlo = xoff + p0, xhi = xoff + p0 + ngrp * UC - 1;
+    const long long ylo = YPADL + yoff + d0 - p0 - ngrp * UC + 1, yhi = YPADL + yoff + d0 - p0 + UC - 1;
     if (!HK_CHECK(p.st, xlo >= 0 && xhi < xlim, 6, xhi, xlim) ||
         !HK_CHECK(p.st, ylo >= ymin && yhi < ylim, 7, ylo < ymin ? ylo : yhi, ylim) ||
         !HK_CHECK(p.st, crow * p.C + p.C <= p.colsum_len, 8, crow * p.C + p.C, p.colsum_len))
@@ -338,7 +342,7 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
       for (int m = 1; m < UC; m++) wb[m] = Y[d0 + m - p0];
       if (!neg) {
 #pragma unroll 1
-        for (int b = 0; b < p.upc / UC; b++) {
+        for (int b = 0; b < ngrp; b++) {
           const int pb = p0 + b * UC;
           const uint4 xa = *reinterpret_cast<const uint4 *>(X + pb);
           const uint4 xb = *reinterpret_cast<const uint4 *>(X + pb + 4);
@@ -352,7 +356,7 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
         }
       } else {
 #pragma unroll 1
-        for (int b = 0; b < p.upc / UC; b++) {
+        for (int b = 0; b < ngrp; b++) {
           const int pb = p0 + b * UC;
           const uint4 xa = *reinterpret_cast<const uint4 *>(X + pb);
           const uint4 xb = *reinterpret_cast<const uint4 *>(X + pb + 4);
@@ -602,12 +606,40 @@ int build_units(const SubProb *sub, int nsub, int uc, int upc, Unit *out, int ca
       len[s] = hi >= lo ? hi - lo + 1 : 0;
       kmax = std::max(kmax, (len[s] + upc - 1) / upc);
     }
+    if (uc != 8) {
+      for (int k = 0; k < kmax; k++)
+        for (int s = 0; s < S; s++)
+          if (k * upc < len[s]) {
+            if (out && n < cap) out[n] = Unit{(q << 24) | (s * uc), plo[s] + k * upc};
+            n++;
+          }
+      continue;
+    }
+    // stripe 8: full chunks of upc p-steps, then each stripe's remainder as a
+    // shorter chunk rounded up to eight steps (its length in bits 16..23 of
+    // p0, in groups of eight); the remainders follow the full chunks, longest
+    // first, so that the lanes of a warp mostly share one length
     for (int k = 0; k < kmax; k++)
       for (int s = 0; s < S; s++)
-        if (k * upc < len[s]) {
-          if (out && n < cap) out[n] = Unit{(q << 24) | (s * uc), plo[s] + k * upc};
+        if ((k + 1) * upc <= len[s]) {
+          if (out && n < cap) out[n] = Unit{(q << 24) | (s * uc), (plo[s] + k * upc) | ((upc / 8) << 16)};
           n++;
         }
+    for (int r = upc; r > 0; r -= 8)
+      for (int s = 0; s < S; s++) {
+        const int rem = len[s] % upc;
+        if (rem > 0 && (rem + 7) / 8 * 8 == r) {
+          if (out && n < cap) out[n] = Unit{(q << 24) | (s * uc), (plo[s] + (len[s] / upc) * upc) | ((r / 8) << 16)};
+          n++;
+        }
+      }
+  }
+  if (uc == 8 && out && n <= cap) {
+    // within each block (its units keep their operand window), longest units
+    // first, so that a warp's lanes share one length
+    for (int b0 = 0; b0 < n; b0 += UNT)
+      std::stable_sort(out + b0, out + std::min(n, b0 + UNT),
+                       [](const Unit &a, const Unit &b) { return ((a.p0 >> 16) & 0xff) > ((b.p0 >> 16) & 0xff); });
   }
   return n;
 }
@@ -644,6 +676,20 @@ static const double kSpeed[4] = {41.7, 52.8, 45.9, 45.1};
 static double schedule_cost(const SubProb *sub, int nsub, int ui, int upc) {
   const int uc = kUcs[ui];
   const int n = build_units(sub, nsub, uc, upc, nullptr, 0);
+  if (uc == 8) {
+    // chunks of their own lengths: a warp costs its longest lane; idle
+    // warps of the last block cost nothing (the other blocks of the SM fill
+    // the integer pipe)
+    std::vector<Unit> h(n);
+    build_units(sub, nsub, uc, upc, h.data(), n);
+    double slots = 0;
+    for (int w0 = 0; w0 < n; w0 += 32) {
+      int mx = 0;
+      for (int u = w0; u < std::min(n, w0 + 32); u++) mx = std::max(mx, (h[u].p0 >> 16) & 0xff);
+      slots += 32.0 * mx * 8 * uc;
+    }
+    return (slots + (double)n * 1.75 * uc) / kSpeed[ui];
+  }
   const int blocks = (n + UNT - 1) / UNT;
   return ((double)blocks * UNT * upc * uc + (double)n * 1.75 * uc) / kSpeed[ui];
 }

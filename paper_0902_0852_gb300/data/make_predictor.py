@@ -9,9 +9,15 @@ kernels).  Writes, into --out (default: this directory):
                          and verified solve (precisions, seconds, agreement)
 
 Instances: training N ~ U{32..512}, beta ~ U[0.6, 4] snapped to the rational
-grid of predictor.beta_grid() (seed 1); held-out N ~ U{513..800}, same beta
-law (seed 2).
+grid of predictor.beta_grid() (seed 1, 4096 instances); held-out N ~ U{513..800},
+same beta law (seed 2, 256 instances).
+
+The generation can run in pieces: ``--range A:B`` generates the tuples of
+training instances A..B-1 only (into predictor_tuples.partA_B.json), and
+``--merge DIR`` joins the part files found in DIR (they must cover 0..train-1)
+before training and the held-out evaluation.
 """
+import glob
 import argparse
 import json
 import os
@@ -30,8 +36,10 @@ def log(msg):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--train", type=int, default=1024)
-    ap.add_argument("--heldout", type=int, default=64)
+    ap.add_argument("--train", type=int, default=4096)
+    ap.add_argument("--heldout", type=int, default=256)
+    ap.add_argument("--range", default=None, help="A:B -- generate the tuples of training instances A..B-1 only")
+    ap.add_argument("--merge", default=None, help="join the part files in this directory, then train and evaluate")
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--out", default=HERE)
     ap.add_argument("--tuples", default=None, help="reuse an existing tuples file")
@@ -39,7 +47,33 @@ def main():
     args = ap.parse_args()
     build.build()
     os.makedirs(args.out, exist_ok=True)
-    if args.tuples:
+    if args.range:
+        a, b = (int(v) for v in args.range.split(":"))
+        inst = pr.sample_instances(args.train, 1, 32, 512)[a:b]
+        t0 = time.time()
+        tuples = pr.generate(inst, workers=args.workers, log=log)
+        meta = dict(first=a, last=b, seconds=round(time.time() - t0, 1))
+        with open(os.path.join(args.out, f"predictor_tuples.part{a}_{b}.json"), "w") as f:
+            json.dump(dict(meta=meta, tuples=tuples), f)
+        log(f"{len(tuples)} tuples ({a}..{b - 1}) in {meta['seconds']} s")
+        return
+    if args.merge:
+        parts = []
+        for path in glob.glob(os.path.join(args.merge, "predictor_tuples.part*_*.json")):
+            d = json.load(open(path))
+            parts.append((d["meta"]["first"], d["meta"]["last"], d["meta"]["seconds"], d["tuples"]))
+        parts.sort()
+        assert parts and parts[0][0] == 0 and parts[-1][1] == args.train, "parts must cover 0..train-1"
+        assert all(p[1] == q[0] for p, q in zip(parts, parts[1:])), "parts must be contiguous"
+        tuples = [t for p in parts for t in p[3]]
+        meta = dict(generator="paper_0902_0852_gb300/data/make_predictor.py", count=len(tuples), seed=1,
+                    N_range=[32, 512], beta="U[0.6,4] snapped to beta_grid()",
+                    seconds=round(sum(p[2] for p in parts), 1), parts=len(parts),
+                    agree_bits=pr.AGREE_BITS, delta=pr.DELTA)
+        with open(os.path.join(args.out, "predictor_tuples.json"), "w") as f:
+            json.dump(dict(meta=meta, tuples=tuples), f, indent=0)
+        log(f"{len(tuples)} tuples merged from {len(parts)} parts ({meta['seconds']} s of generation)")
+    elif args.tuples:
         tuples = json.load(open(args.tuples))["tuples"]
     else:
         inst = pr.sample_instances(args.train, 1, 32, 512)

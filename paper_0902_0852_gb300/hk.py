@@ -554,7 +554,15 @@ def hk_update_plan(W, levels=-1, with_units=True):
         ub = (ctypes.c_int32 * (2 * nunits))()
         wb = (ctypes.c_int32 * (2 * 64))()
         _check(L.hk_update_plan(W, levels, info, None, None, None, ub, nunits, wb), "hk_update_plan")
-        units = [(ub[2 * u] >> 24, ub[2 * u] & 0xFFFFFF, ub[2 * u + 1]) for u in range(nunits)]
+        # (piece, first column, first p, p-steps); stripe-8 units carry their own
+        # length (groups of eight in bits 16..23 of the start), others the chunk
+        units = []
+        for u in range(nunits):
+            q, d0, pw = ub[2 * u] >> 24, ub[2 * u] & 0xFFFFFF, ub[2 * u + 1]
+            if info[4] == 8:
+                units.append((q, d0, pw & 0xFFFF, ((pw >> 16) & 0xFF) * 8))
+            else:
+                units.append((q, d0, pw, info[5]))
         win = [(wb[2 * b], wb[2 * b + 1]) for b in range(nxb)]
     return {
         "levels": info[0], "npieces": n, "stride": info[2], "gap": info[3], "uc": info[4], "upc": info[5],

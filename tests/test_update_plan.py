@@ -82,8 +82,9 @@ def test_units_cover_every_product_once(hk, W, levels):
     assert upc % uc == 0
     widths = [w for _, w in plan["pieces"]] if plan["levels"] > 0 else [W]
     counts = [np.zeros((w + upc, 2 * w + uc), dtype=np.int32) for w in widths]
-    for q, d0, p0 in plan["units"]:
-        counts[q][p0:p0 + upc, d0:d0 + uc] += 1
+    for q, d0, p0, ln in plan["units"]:
+        assert ln % uc == 0 and 0 < ln <= upc
+        counts[q][p0:p0 + ln, d0:d0 + uc] += 1
     for w, c in zip(widths, counts):
         p = np.arange(w + upc)[:, None]
         d = np.arange(2 * w + uc)[None, :]
@@ -96,11 +97,11 @@ def test_unit_reads_stay_in_gaps_and_windows(hk, W, levels):
     plan = hk.hk_update_plan(W, levels)
     uc, upc, G = plan["uc"], plan["upc"], plan["gap"]
     pieces = plan["pieces"] if plan["levels"] > 0 else [(0, W)]
-    for u, (q, d0, p0) in enumerate(plan["units"]):
+    for u, (q, d0, p0, ln) in enumerate(plan["units"]):
         off, w = pieces[q]
-        # X limbs p0 .. p0 + upc - 1, Y limbs d - p over the stripe and chunk
-        xlo, xhi = p0, p0 + upc - 1
-        ylo, yhi = d0 - (p0 + upc - 1), d0 + uc - 1 - p0
+        # X limbs p0 .. p0 + ln - 1, Y limbs d - p over the stripe and chunk
+        xlo, xhi = p0, p0 + ln - 1
+        ylo, yhi = d0 - (p0 + ln - 1), d0 + uc - 1 - p0
         assert 0 <= xlo < w
         if uc == 8:
             assert p0 % 4 == 0 and off % 4 == 0  # X read as aligned quads
