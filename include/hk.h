@@ -305,6 +305,14 @@ int hk_time_update_slice(hk_ctx *ctx, int tsteps, double *ms, double *macs);
 int hk_selftest_mp(int op, int L, const uint32_t *x, int nx, int64_t ex,
                    const uint32_t *y, int ny, int64_t ey, uint32_t *out, int64_t *eo);
 
+/* Self-test of the scalar P-bit operations of the Secant recurrence (the
+ * kernels behind hk_secant), on host values of L limbs (copied in and out,
+ * on a private stream): op 0: *out = RNE(a - b) (exact difference, rounded
+ * once; an operand more than P + 64 bits below the other enters as a sticky
+ * unit), op 1: *out = RNE(a b), op 2: *out = RNE(a / b) (b nonzero),
+ * op 3: *cmp = -1, 0 or 1 as a < b, a = b, a > b (exact comparison). */
+int hk_selftest_scalar(int op, int L, const hk_mp *a, const hk_mp *b, hk_mp *out, int *cmp);
+
 /* ----- allocation-free multiprecision operation ----------------------------
  * The paper has no counterpart: this is a service for callers that must not
  * allocate device memory -- code whose device memory is owned by another

@@ -2113,4 +2113,50 @@ int hk_time_update_slice(hk_ctx *c, int tsteps, double *ms, double *macs) {
   return HK_OK;
 }
 
+
+int hk_selftest_scalar(int op, int L, const hk_mp *a, const hk_mp *b, hk_mp *out, int *cmp) {
+  if (op < 0 || op > 3 || L < 1 || L > HK_MAX_P / 32 || !mp_ok(a) || !mp_ok(b)) return HK_ERR_ARG;
+  if (op < 3 && (!out || !out->limbs)) return HK_ERR_ARG;
+  if (op == 3 && !cmp) return HK_ERR_ARG;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return HK_ERR_CUDA;
+  MpArr da{}, db{}, dout{};
+  void *work = nullptr;
+  int *flags = nullptr;
+  std::vector<void *> owned;
+  auto get = [&](void **p, size_t bytes) {
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) owned.push_back(*p);
+    return e;
+  };
+  cudaError_t e = cudaSuccess;
+  for (MpArr *m : {&da, &db, &dout}) {
+    if (e == cudaSuccess) e = get(reinterpret_cast<void **>(&m->sign), 4);
+    if (e == cudaSuccess) e = get(reinterpret_cast<void **>(&m->exp), 8);
+    if (e == cudaSuccess) e = get(reinterpret_cast<void **>(&m->limbs), 4 * (size_t)L);
+  }
+  if (e == cudaSuccess) e = get(&work, scalar_work_bytes(L));
+  if (e == cudaSuccess) e = get(reinterpret_cast<void **>(&flags), 16);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 16, s);
+  MpArr ha{const_cast<int32_t *>(&a->sign), reinterpret_cast<long long *>(const_cast<int64_t *>(&a->exp)),
+           const_cast<uint32_t *>(a->limbs)};
+  MpArr hb{const_cast<int32_t *>(&b->sign), reinterpret_cast<long long *>(const_cast<int64_t *>(&b->exp)),
+           const_cast<uint32_t *>(b->limbs)};
+  if (e == cudaSuccess) e = copy_entry(da, 0, ha, 0, L, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = copy_entry(db, 0, hb, 0, L, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_scalar_selftest(op, da, db, dout, L, work, flags, s);
+  int hf[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess && op < 3) {
+    MpArr ho{&out->sign, reinterpret_cast<long long *>(&out->exp), out->limbs};
+    e = copy_entry(ho, 0, dout, 0, L, cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hf, flags, 16, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  for (void *p : owned) cudaFree(p);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) return HK_ERR_CUDA;
+  if (op == 3) *cmp = hf[0];
+  return hf[1] ? HK_ERR_TIMEOUT : HK_OK;
+}
+
 }  // extern "C"

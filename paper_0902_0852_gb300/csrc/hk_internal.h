@@ -175,6 +175,8 @@ cudaError_t launch_secant_step(MpArr xs, MpArr ps, MpArr tmpv, int k1, int k2, i
 cudaError_t launch_neg_min_pivot(MpArr R, int N, int L, MpArr dst, int kd, cudaStream_t s);
 cudaError_t launch_scale_pm(MpArr src, int ks, int L, int bits, int sgn, MpArr dst, int kd, int L2, cudaStream_t s);
 cudaError_t launch_widen(MpArr src, int n, int L, MpArr dst, int L2, cudaStream_t s);
+cudaError_t launch_scalar_selftest(int op, MpArr a, MpArr b, MpArr out, int L, void *work, int *flags,
+                                  cudaStream_t s);
 
 // ---- solve kernels (hk_solve.cu) -------------------------------------------------
 struct SolveParams {

@@ -493,6 +493,26 @@ __global__ void __launch_bounds__(NT) k_secant_step(MpArr xs, MpArr ps, MpArr tm
   if (threadIdx.x == 0) flags[2] = conv;
 }
 
+// Self-test of the Secant step's scalar operations on one pair of values:
+// op 0: RNE(a - b), 1: RNE(a * b), 2: RNE(a / b) (b nonzero), 3: the exact
+// comparison of a and b (-1, 0, 1 in flags[0]).
+template <int NT>
+__global__ void __launch_bounds__(NT) k_scalar_selftest(int op, MpArr a, MpArr b, MpArr out, int L, ScalarWork sw,
+                                                        int *flags) {
+  __shared__ mp::Red red;
+  mp::Work w;
+  w.cs = sw.cs;
+  w.tmp = sw.tmp;
+  w.r = &red;
+  if (op == 0) add_rne<NT>(a, 0, b, 0, 1, out, 0, L, sw, w);
+  if (op == 1) mul_rne<NT>(a, 0, b, 0, out, 0, L, sw, w);
+  if (op == 2) {
+    const bool ok = div_rne_val<NT>(a, 0, b, 0, out, 0, L, sw, w);
+    if (threadIdx.x == 0) flags[1] = ok ? 0 : 1;
+  }
+  if (op == 3 && threadIdx.x == 0) flags[0] = cmp_val(a, 0, b, 0, L);
+}
+
 // Smallest pivot (reading of the paper's start x_1 < 0): dst[kd] = -min_t D_t
 // over the diagonal of the packed triangle R (exact comparisons).
 template <int NT>
@@ -633,6 +653,12 @@ static ScalarWork scalar_work(void *base, int L) {
 cudaError_t launch_secant_step(MpArr xs, MpArr ps, MpArr tmpv, int k1, int k2, int k3, int kstep, int have_last,
                                int L, void *work, int *flags, cudaStream_t s) {
   k_secant_step<NT_SC><<<1, NT_SC, 0, s>>>(xs, ps, tmpv, k1, k2, k3, kstep, have_last, L, scalar_work(work, L), flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scalar_selftest(int op, MpArr a, MpArr b, MpArr out, int L, void *work, int *flags,
+                                  cudaStream_t s) {
+  k_scalar_selftest<NT_SC><<<1, NT_SC, 0, s>>>(op, a, b, out, L, scalar_work(work, L), flags);
   return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ EXPORTS = [
     "hk_mlp_workspace_bytes", "hk_mlp_forward", "hk_mlp_loss_grad", "hk_mlp_adam", "hk_mlp_train",
     "hk_set_predictor", "hk_predict", "hk_update_plan", "hk_selftest_wait",
     "hk_ldlt_det", "hk_get_ldlt_flat", "hk_secant", "hk_get_secant_flat", "hk_secant_verify",
-    "hk_time_update_slice",
+    "hk_time_update_slice", "hk_selftest_scalar",
 ]
 
 
@@ -95,6 +95,8 @@ def lib():
         L.hk_get_secant_flat.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
         L.hk_secant_verify.argtypes = [vp, ctypes.POINTER(HkMp), i32, i32, ctypes.POINTER(i32)]
         L.hk_time_update_slice.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        L.hk_selftest_scalar.argtypes = [i32, i32, ctypes.POINTER(HkMp), ctypes.POINTER(HkMp), ctypes.POINTER(HkMp),
+                                         ctypes.POINTER(i32)]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype if name in ("hk_destroy", "hk_strerror") else i32
         L.hk_mlp_workspace_bytes.restype = sz
@@ -385,6 +387,18 @@ def hk_time_update_slice(ctx, tsteps):
     ms, macs = ctypes.c_double(0), ctypes.c_double(0)
     _check(lib().hk_time_update_slice(ctx, tsteps, ctypes.byref(ms), ctypes.byref(macs)), "hk_time_update_slice")
     return ms.value, macs.value
+
+
+def hk_selftest_scalar(op, P, a, b):
+    """Scalar operation of the Secant step on the device: op 0 RNE(a - b),
+    1 RNE(a b), 2 RNE(a / b) -> (n, e); op 3 -> comparison -1/0/1."""
+    am, al = _mp_in(a, P)
+    bm, bl = _mp_in(b, P)
+    om, ol = _mp_out(P)
+    cmp = ctypes.c_int(0)
+    _check(lib().hk_selftest_scalar(op, P // 32, ctypes.byref(am), ctypes.byref(bm), ctypes.byref(om),
+                                    ctypes.byref(cmp)), "hk_selftest_scalar")
+    return cmp.value if op == 3 else _mp_val(om, ol)
 
 
 def hk_ldlt_det(ctx, P, x):

@@ -108,3 +108,35 @@ def test_secant_arguments(hk):
         with pytest.raises(hk.HKError) as ei:
             hk.hk_secant_verify(h.ctx, P, (1 << (P - 1), -P), 130, P)  # P2 too small
         assert ei.value.code == hk.HK_ERR_ARG
+
+
+def _rand_val(rng, P, elo, ehi):
+    m = rng.getrandbits(P) | (1 << (P - 1))
+    return (m if rng.random() < 0.5 else -m, rng.randrange(elo, ehi))
+
+
+def test_secant_scalar_ops_against_exact_rounding(hk):
+    """The scalar kernels of the Secant step (exact subtraction rounded once,
+    with a sticky unit for an operand more than P + 64 bits below the other;
+    product; guard-bit division; exact comparison) against the oracle's
+    rounding of the exact results, for operands from equal exponents to
+    exponent gaps far beyond the precision."""
+    import random
+    rng = random.Random(11)
+    for P in (64, 256, 1024):
+        cases = []
+        for gap in (0, 1, 3, 31, P - 1, P, P + 1, P + 63, P + 64, P + 65, P + 200, 5 * P):
+            a = _rand_val(rng, P, -50, 50)
+            b = (_rand_val(rng, P, 0, 1)[0], a[1] - gap)
+            cases += [(a, b), (b, a)]
+        a = _rand_val(rng, P, -20, 20)
+        cases += [(a, a), (a, (-a[0], a[1])), (a, (0, 0)), ((0, 0), a)]
+        # a near-cancellation: b = a - one unit in the last place
+        cases.append((a, (a[0] - (1 if a[0] > 0 else -1), a[1])))
+        for a, b in cases:
+            assert hk.hk_selftest_scalar(0, P, a, b) == S.mp_sub(a, b, P), (P, a[1] - b[1])
+            assert hk.hk_selftest_scalar(1, P, a, b) == S.mp_mul(a, b, P)
+            if b[0] != 0:
+                assert hk.hk_selftest_scalar(2, P, a, b) == oracle.mp_div(a, b, P)
+            fa, fb = oracle.to_fraction(a), oracle.to_fraction(b)
+            assert hk.hk_selftest_scalar(3, P, a, b) == (fa > fb) - (fa < fb)

@@ -87,6 +87,7 @@ def test_every_entry_point_rejects_a_null_context_or_bad_argument(lib):
         lambda: lib.hk_get_secant_flat(None, 0, None, None, None, None, None, None),
         lambda: lib.hk_secant_verify(None, None, 130, 512, None),
         lambda: lib.hk_time_update_slice(None, 16, None, None),
+        lambda: lib.hk_selftest_scalar(9, 1, None, None, None, None),
     ]
     for k, call in enumerate(calls):
         assert call() == ARG, k
