@@ -33,7 +33,7 @@ SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.act
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 # DRAM bytes (read + write) per executed limb product of the update kernel, from
 # one ncu capture of the current kernel version; None when not measured.
-UPDATE_TRAFFIC_BYTES_PER_LIMBPROD = None  # the update kernel changed since the last DRAM capture
+UPDATE_TRAFFIC_BYTES_PER_LIMBPROD = (8.395456e9 + 0.0322035e9) / (3976 * 256 * 265833)  # k_update_stripe8_N512_P24576_full.md
 
 
 def parse():
