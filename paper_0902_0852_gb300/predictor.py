@@ -354,6 +354,59 @@ def _solve_one(h, N, beta, P, T):
     return lam, used, conv, time.perf_counter() - t0
 
 
+def _solve_loaded(h, N, beta, P, m, T):
+    """_solve_one with the moments already generated."""
+    t0 = time.perf_counter()
+    h.load(N, beta, P, m)
+    try:
+        h.factor()
+    except hk.HKError as e:
+        if e.code == hk.HK_ERR_NOT_PD:
+            return None, 0, False, time.perf_counter() - t0
+        raise
+    hk.hk_set_option(h.ctx, hk.HK_OPT_MAX_ITERS, T)
+    lam, used = h.smallest_eig(0)
+    conv = bool(h.stats()["converged"])
+    return lam, used, conv, time.perf_counter() - t0
+
+
+def _solve_pair(N, beta, Ps, T):
+    """Independent solves at the precisions Ps at the same time: one context
+    per precision on its own non-blocking stream, driven by its own host
+    thread (the library calls release the interpreter lock), so that the
+    sequential per-row kernels of one overlap the other's.  Moments are
+    generated first, outside the timed span.  Returns the per-solve results
+    and the wall time of the pair."""
+    import threading
+    import torch
+    ms = [inputs.moments(N, beta, P) for P in Ps]
+    streams = [torch.cuda.Stream() for _ in Ps]
+    hs = [hk.Hankel(0, st) for st in streams]
+    out = [None] * len(Ps)
+    err = []
+
+    def run(k):
+        try:
+            out[k] = _solve_loaded(hs[k], N, beta, Ps[k], ms[k], T)
+        except Exception as e:  # re-raised in the caller's thread
+            err.append(e)
+
+    try:
+        t0 = time.perf_counter()
+        ths = [threading.Thread(target=run, args=(k,)) for k in range(len(Ps))]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        wall = time.perf_counter() - t0
+    finally:
+        for h in hs:
+            h.close()
+    if err:
+        raise err[0]
+    return out, wall
+
+
 def solve_conservative(N, beta, T=MAX_ITERS):
     """The method without the predictor: one solve at the conservative P."""
     P = p_conservative(N, beta)
@@ -369,22 +422,28 @@ def solve_verified(N, beta, predictor=None, P=None, T=MAX_ITERS, max_escalations
     defaults to the conservative rule.  The solve at P is accepted when a
     rerun at P + 1024 converges to a value within 2^-128 (relative) of it;
     otherwise P grows by 1024 (and T doubles when the iteration did not
-    converge) and the check repeats.  Returns a dict with the accepted lambda
-    (the P + 1024 value), the precisions tried and the library seconds spent
-    (moment generation excluded)."""
+    converge) and the check repeats.  The first solve and its check run at the
+    same time on two streams.  Returns a dict with the accepted lambda (the
+    P + 1024 value), the precisions tried and the seconds spent in the library
+    (wall time; moment generation excluded)."""
     if predictor is not None:
         P, T, _ = predictor.predict(N, beta)
     elif P is None:
         P = p_conservative(N, beta)
     tried = []
     sec = 0.0
+    # the solve at P and its check at P + DELTA are independent: run them at
+    # the same time (wall time counted once)
+    (lo, hi0), wall = _solve_pair(N, beta, [P, P + DELTA], T)
+    sec += wall
+    tried.append(P)
     with hk.Hankel(0) as h:
-        lo = _solve_one(h, N, beta, P, T)
-        sec += lo[3]
-        tried.append(P)
-        for _ in range(max_escalations + 1):
-            hi = _solve_one(h, N, beta, P + DELTA, T)
-            sec += hi[3]
+        for rnd in range(max_escalations + 1):
+            if rnd == 0:
+                hi = hi0
+            else:
+                hi = _solve_one(h, N, beta, P + DELTA, T)
+                sec += hi[3]
             tried.append(P + DELTA)
             if lo[0] is not None and hi[0] is not None and lo[2] and hi[2]:
                 if rel_err_bits(lo[0], hi[0]) >= AGREE_BITS:

@@ -67,12 +67,14 @@ def test_batch_escalates_too_small_precision(hk):
 
 
 def test_batched_sweep_subset_against_oracle(hk):
-    """The two smallest instances of the batched sweep (seed 0), with the sweep's
-    precision rule and escalation, against the oracle at the final precision."""
+    """The four smallest instances of the batched sweep (seed 0: N = 101, 102,
+    104, 108; beta = 1, 3/4, 2, 1), with the sweep's precision rule and
+    escalation, against the oracle at the final precision."""
     from paper_0902_0852_gb300 import batch
-    inst = sorted(inputs.batched_instances(64, 0), key=lambda x: x[0])[:2]
+    inst = sorted(inputs.batched_instances(64, 0), key=lambda x: x[0])[:4]
     T = 6
-    res = batch.solve_batch(inst, iters=T, nthreads=2)
+    res = batch.solve_batch(inst, iters=T, nthreads=4)
+    assert len(res) == 4
     for r in res:
         assert r["status"] == hk.HK_OK
         m = inputs.moments(r["N"], r["beta"], r["P"])
