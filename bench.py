@@ -50,7 +50,29 @@ def parse():
                     help="skip the predicted-precision time-to-lambda comparison (after the timed region)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the after-region comparisons (Secant, INT8 update, batched sweep)")
+    ap.add_argument("--paper-cells", default=None, metavar="N:p/q,...|default",
+                    help="instead of the bench: Table 3 cells at a verified precision, one JSON line")
     return ap.parse_args()
+
+
+def run_paper_cells(spec):
+    """Table 3 cells (N, beta) on the device at a verified precision."""
+    from paper_0902_0852_gb300 import build
+    from paper_0902_0852_gb300.paper_cells import DEFAULT_CELLS, run_cell
+    build.build()
+    if spec == "default":
+        cells = DEFAULT_CELLS
+    else:
+        cells = []
+        for item in spec.split(","):
+            n, b = item.split(":")
+            p, q = b.split("/")
+            cells.append((int(n), (int(p), int(q))))
+    out = []
+    for N, beta in cells:
+        out.append(run_cell(N, beta))
+        print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"paper_cells": out, "matched": sum(r["match"] for r in out), "cells": len(out)}))
 
 
 def step_macs(N, T):
@@ -238,6 +260,9 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.paper_cells:
+        run_paper_cells(args.paper_cells)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

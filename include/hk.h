@@ -117,7 +117,7 @@ int hk_set_update_path(hk_ctx *ctx, int path);
 
 /* Options of a context (take effect at the next hk_factor):
  *   HK_OPT_UPDATE_PATH      0 IMAD product scanning (default), 1 INT8 mma.sync
- *   HK_OPT_KARATSUBA        Karatsuba levels of the IMAD update, 0..3, or -1
+ *   HK_OPT_KARATSUBA        Karatsuba levels of the IMAD update, 0..4, or -1
  *                           (default): the depth of least modelled update
  *                           cost for the window width
  *   HK_OPT_GRAPH            1: capture each factorisation's launch sequence in a
@@ -140,7 +140,10 @@ int hk_set_update_path(hk_ctx *ctx, int path);
  *                           priority stream), the update of block b + 1 by all
  *                           rows up to block b - 1 runs on a low-priority
  *                           stream, and only the contribution of block b waits
- *                           for its panel; 0: one stream, strictly in order
+ *                           for its panel; in the solves of hk_smallest_eig
+ *                           the GEMV of block b + 1 against the entries known
+ *                           before block b runs beside block b's entry chain
+ *                           the same way; 0: one stream, strictly in order
  * None of the first five, nor the lookahead, changes any result: every sum is
  * exact. */
 enum { HK_OPT_UPDATE_PATH = 0, HK_OPT_KARATSUBA = 1, HK_OPT_GRAPH = 2, HK_OPT_AUTOTUNE = 3, HK_OPT_PANEL_ROWS = 4,
@@ -265,7 +268,11 @@ int hk_get_timings(hk_ctx *ctx, double *out, int n);
  * out[7] the largest and mean window width in limbs of the solution vectors
  * in that hk_smallest_eig (the exact products of a solve cost W x that width),
  * out[8] how many window widenings of the last hk_factor resumed at the
- * failing block (re-aligning the finished rows) instead of restarting. */
+ * failing block (re-aligning the finished rows) instead of restarting,
+ * out[9] and out[10] how many solve blocks of that hk_smallest_eig used the
+ * GEMV the lookahead prepared for them, and how many prepared GEMVs were
+ * dropped because the block's vector range did not fit their grid.
+ * n = number of int64 provided (entries past 10 are set to 0). */
 int hk_get_stats(hk_ctx *ctx, int64_t *out, int n);
 
 /* ----- measurement hook ------------------------------------------------------
@@ -381,25 +388,28 @@ int hk_mlp_train(float *params, float *m, float *v, float *grad, const float *x,
  * Karatsuba pieces (lo, hi, lo + hi of a split, recursively), contracts piece k
  * of the X entries with piece k of the Y entries exactly, and adds that
  * contraction to the result at each of its terms (offset in limbs, sign).
- *   levels     Karatsuba depth 0..3, or -1 for the depth of least modelled
- *              update cost (the hk_factor default)
+ *   levels     Karatsuba depth 0..4, or -1 for the depth of least modelled
+ *              update cost (the hk_factor default); windows below 64 limbs
+ *              take at most three levels
  *   info[9]    out: [0] depth, [1] pieces n, [2] expanded entry stride in
  *              limbs, [3] zero gap between pieces (limbs), [4] stripe width
  *              uc, [5] chunk length upc, [6] units, [7] blocks per output with
  *              their own operand window (0: blocks stage whole entries), [8]
  *              column-sum width C
- *   splits[13] out (may be NULL): level-1 split m1, level-2 splits of the lo,
- *              hi, lo+hi pieces, level-3 splits of the nine level-2 pieces
- *              (unused levels 0)
- *   pieces     out (may be NULL, 3 x 27 ints): per piece k < n its offset in
+ *   splits[40] out (may be NULL): the split points level by level -- [0] the
+ *              level-1 split, [1..4) the level-2 splits of the lo, hi, lo+hi
+ *              pieces, [4..13) the level-3 splits of the nine level-2 pieces,
+ *              [13..40) the level-4 splits of the 27 level-3 pieces (unused
+ *              levels 0)
+ *   pieces     out (may be NULL, 3 x 81 ints): per piece k < n its offset in
  *              the expanded entry, width, number of terms
- *   terms      out (may be NULL, 2 x 8 x 27 ints): term t of piece k at
- *              [2(8k + t)] (offset in limbs) and [2(8k + t) + 1] (sign +-1)
+ *   terms      out (may be NULL, 2 x 16 x 81 ints): term t of piece k at
+ *              [2(16k + t)] (offset in limbs) and [2(16k + t) + 1] (sign +-1)
  *   units      out (may be NULL, 2 x ucap ints): unit u = (piece << 24 |
  *              first result column of its stripe, first p of its chunk)
  *   win        out (may be NULL, 2 x 64 ints): block b's operand window
  *              (first limb, limbs) within the expanded entry
- * Returns HK_ERR_ARG for W < 1, levels outside -1..3, a NULL info, or ucap
+ * Returns HK_ERR_ARG for W < 1, levels outside -1..4, a NULL info, or ucap
  * below the unit count when units is given. */
 int hk_update_plan(int W, int levels, int64_t *info, int32_t *splits, int32_t *pieces, int32_t *terms,
                    int32_t *units, int64_t ucap, int32_t *win);

@@ -55,6 +55,7 @@ struct EvPair {
 // unit table and schedule of the update kernel for one operand shape
 struct Sched {
   Unit *units;
+  SubProb *dsub;  // device copy of sub
   int n, uc, upc;
   int nsub;
   SubProb sub[MAX_SUB];
@@ -117,6 +118,12 @@ struct hk_ctx {
   MpArr v{}, y{}, w{}, hist{};
   int hist_cap = 0, hist_count = 0;
   uint32_t *vecA = nullptr, *vecB = nullptr;
+  // second vector set of the solve lookahead: the next block's far GEMV is
+  // prepared in it while the current block's entries are computed
+  uint32_t *vecA2 = nullptr, *vecA2exp = nullptr;
+  int32_t *vecA2sign = nullptr;
+  long long *colsum_s2 = nullptr;
+  long long pf_hits = 0, pf_miss = 0;  // prepared GEMVs used / dropped in the last eig
   uint32_t *vecAexp = nullptr;  // Karatsuba expansion of vecA (solves on the factor's window)
   size_t vecAexp_cap = 0;       // limbs
   int32_t *vecAsign = nullptr, *vecBsign = nullptr;
@@ -135,13 +142,15 @@ struct hk_ctx {
   int resumes = 0;  // widenings that resumed at a later block instead of restarting
   long long top_margin = 0;  // extra bits above the a priori column bounds
   bool timing = true;
-  // shifted LDL^T of M - xI (the paper's determinant), Secant and verification
   // lookahead: the far part of the next block's update (rows two blocks back and
   // earlier) runs on a low-priority stream while the current block's
-  // sequential panel chain runs on a high-priority one
+  // sequential panel chain runs on a high-priority one; in the solves, the next
+  // block's GEMV against all but the current block's entries
   bool lookahead = true;
   cudaStream_t la_hi = nullptr, la_lo = nullptr;
   std::vector<cudaEvent_t> la_ev;
+  cudaEvent_t sv_fork = nullptr, sv_done = nullptr, sv_join = nullptr;
+  // shifted LDL^T of M - xI (the paper's determinant), Secant and verification
   bool ldl_mode = false;     // the factor driver runs the LDL^T instead of Cholesky
   Arena ldl_arena, ldl_small;
   MpArr Qf{};                // CDivDiag in floating form
@@ -304,6 +313,7 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
   long long *cs = nullptr;
   DevStatus *st = nullptr;
   Unit *units = nullptr;
+  SubProb *dsub = nullptr;
   const int C = colsum_width(sub, nsub, 7) + 64;
   long long nout = 0;
   for (int i = r0; i < r1; i++) nout += Nt - i;
@@ -311,6 +321,9 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
             cudaMalloc(&cs, (size_t)nout * C * 8 * 2) == cudaSuccess && cudaMalloc(&st, sizeof(DevStatus)) == cudaSuccess;
   const int cap = build_units(sub, nsub, 7, 14, nullptr, 0) + 16;  // the most units of any candidate
   ok = ok && cudaMalloc(&units, (size_t)cap * sizeof(Unit)) == cudaSuccess;
+  ok = ok && cudaMalloc(&dsub, (size_t)nsub * sizeof(SubProb)) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(dsub, sub, (size_t)nsub * sizeof(SubProb), cudaMemcpyHostToDevice, c->stream) ==
+                 cudaSuccess;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ok) {
     k_fill_random<<<256, 256, 0, c->stream>>>(A, NTt * stride, 12345u);
@@ -343,7 +356,7 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
       up.uc = uc;
       up.upc = upc;
       up.nsub = nsub;
-      for (int k = 0; k < nsub; k++) up.sub[k] = sub[k];
+      up.sub = dsub;
       up.r0 = r0;
       up.ra = r0;
       up.rb = r1;
@@ -382,6 +395,7 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
   cudaFree(cs);
   cudaFree(st);
   cudaFree(units);
+  cudaFree(dsub);
   return ok && best < 1e30f;
 }
 
@@ -471,6 +485,10 @@ cudaError_t sched_for(hk_ctx *c, int Wx, int Wy, int levels, Sched *out) {
   plan_units(sp, Wx, Wy, levels, uc, upc, &sc, &h);
   cudaError_t e = alloc(c, c->base_arena, &sc.units, (size_t)sc.n);
   if (e != cudaSuccess) return e;
+  e = alloc(c, c->base_arena, &sc.dsub, (size_t)sc.nsub);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(sc.dsub, sc.sub, sizeof(SubProb) * sc.nsub, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return e;
   // on the context's stream: a plain cudaMemcpy runs on the legacy default
   // stream, which a non-blocking context stream does not wait for, and for
   // pageable memory it returns before the transfer has landed
@@ -487,7 +505,7 @@ void fill_sched(UpdParams &up, const Sched &sc) {
   up.uc = sc.uc;
   up.upc = sc.upc;
   up.nsub = sc.nsub;
-  for (int k = 0; k < sc.nsub; k++) up.sub[k] = sc.sub[k];
+  up.sub = sc.dsub;
   up.C = sc.C;
   up.nxb = sc.nxb;
   for (int k = 0; k < sc.nxb; k++) {
@@ -539,6 +557,7 @@ __global__ void k_col_grid(int N, const long long *colU, int W, long long *colG)
 
 // one attempt of the blocked factorisation with window width c->W
 int factor_enqueue(hk_ctx *c, const Sched &sc, int r_start);
+cudaError_t ensure_la_streams(hk_ctx *c);
 
 // Karatsuba depth of the factor update for the current window: the option's
 // value, or the depth of least modelled update cost for W
@@ -723,12 +742,7 @@ int factor_enqueue(hk_ctx *c, const Sched &sc, int r_start) {
   const int nblk = (N - r_start + nb - 1) / nb;
   const bool la = c->lookahead && nblk > 2;
   if (la) {
-    if (!c->la_hi) {
-      int lo = 0, hi = 0;
-      CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-      CK(cudaStreamCreateWithPriority(&c->la_hi, cudaStreamNonBlocking, hi));
-      CK(cudaStreamCreateWithPriority(&c->la_lo, cudaStreamNonBlocking, lo));
-    }
+    CK(ensure_la_streams(c));
     const size_t need = 3 * (size_t)nblk + 3;
     while (c->la_ev.size() < need) {
       cudaEvent_t e;
@@ -852,25 +866,33 @@ int ensure_solve_buffers(hk_ctx *c, int hist_need) {
   return HK_OK;
 }
 
+// Vector buffers of the solves (both sets of the lookahead, same capacities).
+// A growth allocates new buffers; the old ones stay allocated until the
+// context's solve arena is released, so a set prepared before a growth stays
+// valid.
 int ensure_vec(hk_ctx *c, int Wv, int Cs, int rows, int kar_stride = 0) {
   const size_t need = (size_t)c->N * Wv;
   if (need > c->vec_cap) {
     const size_t cap = need + need / 4 + 1024;
     CK(alloc(c, c->sol_arena, &c->vecA, cap));
     CK(alloc(c, c->sol_arena, &c->vecB, cap));
+    CK(alloc(c, c->sol_arena, &c->vecA2, cap));
     CK(alloc(c, c->sol_arena, &c->vecAsign, (size_t)c->N));
     CK(alloc(c, c->sol_arena, &c->vecBsign, (size_t)c->N));
+    CK(alloc(c, c->sol_arena, &c->vecA2sign, (size_t)c->N));
     c->vec_cap = cap;
   }
   if (kar_stride > 0 && (size_t)c->N * kar_stride > c->vecAexp_cap) {
     const size_t cap = (size_t)c->N * kar_stride;
     CK(alloc(c, c->sol_arena, &c->vecAexp, cap));
+    CK(alloc(c, c->sol_arena, &c->vecA2exp, cap));
     c->vecAexp_cap = cap;
   }
   const size_t cneed = (size_t)rows * Cs;
   if (cneed > c->colsum_s_cap) {
     const size_t cap = cneed + cneed / 4 + 1024;
     CK(alloc(c, c->sol_arena, &c->colsum_s, cap));
+    CK(alloc(c, c->sol_arena, &c->colsum_s2, cap));
     c->colsum_s_cap = cap;
   }
   return HK_OK;
@@ -887,9 +909,164 @@ int exprange(hk_ctx *c, int n, MpArr v, bool scaled, long long *lo, long long *h
   return HK_OK;
 }
 
+// streams of the factor and solve lookahead (created on first use)
+cudaError_t ensure_la_streams(hk_ctx *c) {
+  if (c->sv_join) return cudaSuccess;
+  int lo = 0, hi = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (e == cudaSuccess && !c->la_hi) e = cudaStreamCreateWithPriority(&c->la_hi, cudaStreamNonBlocking, hi);
+  if (e == cudaSuccess && !c->la_lo) e = cudaStreamCreateWithPriority(&c->la_lo, cudaStreamNonBlocking, lo);
+  if (e == cudaSuccess && !c->sv_fork) e = cudaEventCreateWithFlags(&c->sv_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && !c->sv_done) e = cudaEventCreateWithFlags(&c->sv_done, cudaEventDisableTiming);
+  if (e == cudaSuccess && !c->sv_join) e = cudaEventCreateWithFlags(&c->sv_join, cudaEventDisableTiming);
+  return e;
+}
+
+// One vector set of a solve block: the known entries aligned to the block's
+// grid, their Karatsuba expansion and signs, and the block's column sums
+// (pointers and capacities as allocated when the set was taken).
+struct VecSet {
+  uint32_t *A = nullptr, *Aexp = nullptr;
+  int32_t *sign = nullptr;
+  long long *colsum = nullptr;
+  long long A_len = 0, Aexp_len = 0, colsum_len = 0;
+};
+
+VecSet vec_set(hk_ctx *c, int id) {
+  VecSet s;
+  s.A = id ? c->vecA2 : c->vecA;
+  s.Aexp = id ? c->vecA2exp : c->vecAexp;
+  s.sign = id ? c->vecA2sign : c->vecAsign;
+  s.colsum = id ? c->colsum_s2 : c->colsum_s;
+  s.A_len = (long long)c->vec_cap;
+  s.Aexp_len = (long long)c->vecAexp_cap;
+  s.colsum_len = (long long)c->colsum_s_cap;
+  return s;
+}
+
+// Grid of a solve block: vector entries on [h, h + 32 Wv), Karatsuba depth lv
+// of its GEMV (0: schoolbook), the schedules of the GEMV and of the in-block
+// updates, and the column-sum row width serving both.
+struct SolveGrid {
+  long long h = 0;
+  int Wv = 0, lv = 0, Cs = 0;
+  Sched sc{}, sc0{};
+};
+
+int solve_grid(hk_ctx *c, long long h, long long top, SolveGrid *g) {
+  const int W = c->W;
+  // Karatsuba on the factor's split points when the vector fits the factor's
+  // window W: the block's GEMV contracts the expanded R entries with the known
+  // vector entries, expanded for this block's grid in one parallel launch.
+  // The in-block updates (one new entry at a time) use the plain aligned
+  // operands, so no expansion sits on the per-entry chain.
+  const int Wv_need = std::max(4, round4((top - h + 31) / 32));
+  const bool kar_ok = c->fac_levels > 0 && c->Aexp && c->update_path == 0;
+  g->lv = kar_ok && Wv_need <= W ? c->fac_levels : 0;
+  g->Wv = g->lv > 0 ? W : Wv_need;
+  g->h = h;
+  if (g->Wv > HK_MAX_WV) return HK_ERR_RANGE;  // no shared-memory tile could hold it
+  CK(sched_for(c, W, g->Wv, g->lv, &g->sc));
+  g->sc0 = g->sc;
+  if (g->lv > 0) CK(sched_for(c, W, g->Wv, 0, &g->sc0));
+  g->Cs = std::max(g->sc.C, g->sc0.C);
+  return HK_OK;
+}
+
+// update parameters of a solve GEMV (gemv) or of the in-block updates
+UpdParams solve_upd(hk_ctx *c, const SolveGrid &g, const VecSet &vs, bool back, bool gemv) {
+  const bool kar = gemv && g.lv > 0;
+  UpdParams up;
+  std::memset(&up, 0, sizeof(up));
+  up.wait_ns = c->wait_ns;
+  up.mode = back ? M_GEMV_BACK : M_GEMV_FWD;
+  up.N = c->N;
+  up.A = kar ? c->Aexp : c->A;
+  up.Asign = c->Asign;
+  up.astride = kar ? c->kl.stride : c->W;
+  up.Vy = kar ? vs.Aexp : vs.A;
+  up.Vysign = vs.sign;
+  up.vstride = kar ? c->kl.stride : g.Wv;
+  up.cx = up.astride;
+  up.cy = up.vstride;
+  up.colsum = vs.colsum;
+  up.a_len = kar ? c->Aexp_len : c->A_len;
+  up.vy_len = kar ? vs.Aexp_len : vs.A_len;
+  up.colsum_len = vs.colsum_len;
+  fill_sched(up, kar ? g.sc : g.sc0);
+  up.C = g.Cs;
+  up.st = c->st;
+  return up;
+}
+
+// Enqueue on stream s the exact GEMV of rows [B0, B1) against known entries
+// [t0, t1): align those entries to the grid (and expand them), then contract.
+// The column sums accumulate (the caller zeroes them once per block).
+int solve_gemv(hk_ctx *c, const SolveGrid &g, const VecSet &vs, MpArr out, bool back, int B0, int B1, int t0,
+               int t1, cudaStream_t s) {
+  if (t1 <= t0) return HK_OK;
+  CK(launch_vec_align(t0, t1, out, c->L, c->colG, back ? 1 : 0, g.h, g.Wv, vs.A, vs.sign, c->st, vs.A_len, s));
+  DBG(c, "solve vec_align", B0, g.Wv);
+  c->launches++;
+  if (g.lv > 0) {
+    CK(launch_vec_expand(t0, t1, vs.A, c->kl, vs.Aexp, s));
+    DBG(c, "solve vec_expand", B0, g.Wv);
+    c->launches++;
+  }
+  UpdParams up = solve_upd(c, g, vs, back, true);
+  const long long cta_per_out = (g.sc.n + UNT - 1) / UNT;
+  up.r0 = B0;
+  up.ra = B0;
+  up.rb = B1;
+  up.nout = B1 - B0;
+  up.t0 = t0;
+  up.t1 = t1;
+  up.tchunk = pick_tchunk(t1 - t0, cta_per_out * (B1 - B0), 6LL * sm_count(c) * 3);
+  CK(launch_update(up, s));
+  DBG(c, "gemv/dot update", up.ra, up.t0);
+  c->launches++;
+  return HK_OK;
+}
+
+// The solve's launches run on the high-priority lookahead stream, forked from
+// and joined back to the context's stream (also on an early return).
+struct SolveStreams {
+  hk_ctx *c;
+  cudaStream_t orig;
+  bool on = false;
+  SolveStreams(hk_ctx *ctx) : c(ctx), orig(ctx->stream) {}
+  cudaError_t fork() {
+    cudaError_t e = cudaEventRecord(c->sv_fork, orig);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->la_hi, c->sv_fork, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->la_lo, c->sv_fork, 0);
+    if (e != cudaSuccess) return e;
+    c->stream = c->la_hi;
+    on = true;
+    return cudaSuccess;
+  }
+  ~SolveStreams() {
+    if (!on) return;
+    cudaEventRecord(c->sv_join, c->la_lo);
+    cudaStreamWaitEvent(orig, c->sv_join, 0);
+    cudaEventRecord(c->sv_join, c->la_hi);
+    cudaStreamWaitEvent(orig, c->sv_join, 0);
+    c->stream = orig;
+  }
+};
+
 // one triangular solve: forward (R^T out = rhs) or back (R out = rhs)
+//
+// Blocks of nbs rows; block b's column sums are the exact GEMV of its rows
+// against every known entry, followed by its entries one at a time.  With the
+// lookahead on, the GEMV of block b+1 against the entries known before block b
+// (all but block b's own) runs on a low-priority stream while block b's
+// sequential entry chain runs; block b+1 then adds only block b's rows.  That
+// grid is chosen before block b's entries exist: it is block b's range widened
+// by twice the last block's growth; when block b+1's range does not fit it,
+// the prepared sums are dropped and block b+1 runs in full on its own grid.
+// Either way every column sum is exact, so the entries are the same bits.
 int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
-  const int N = c->N, L = c->L, W = c->W, nbs = c->nbs;
+  const int N = c->N, L = c->L, nbs = c->nbs;
   const long long P = 32LL * L;
   std::vector<std::pair<int, int>> blocks;  // [B0, B1) in processing order
   if (!back) {
@@ -899,11 +1076,17 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
     blocks.push_back({N - 1, N});
     for (int b = N - 1; b > 0; b -= nbs) blocks.push_back({std::max(0, b - nbs), b});
   }
+  const bool la = c->lookahead && blocks.size() > 3;
+  SolveStreams ss(c);
+  if (la) {
+    CK(ensure_la_streams(c));
+    CK(ss.fork());
+  }
   SolveParams sp;
   std::memset(&sp, 0, sizeof(sp));
   sp.N = N;
   sp.L = L;
-  sp.W = W;
+  sp.W = c->W;
   sp.R = c->R;
   sp.recip = c->recip;
   sp.colU = c->colU;
@@ -911,13 +1094,24 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
   sp.out = out;
   sp.back = back ? 1 : 0;
   sp.st = c->st;
+  // the prepared GEMV of the next block
+  struct {
+    bool live = false;
+    int B0 = 0, t0 = 0, t1 = 0;  // the block it serves, the entries it contracted
+    int set = 0;
+    SolveGrid g;
+    VecSet vs;
+  } pf;
+  int cur = 0;  // vector set of the current block
   long long margin = c->solve_margin;  // bits above and below the known entries' range
+  long long prev_lo = LLONG_MAX, prev_hi = LLONG_MIN;  // range known before the last block
+  long long grow_lo = 0, grow_hi = 0;                  // its growth over that block
   for (size_t bi = 0; bi < blocks.size(); bi++) {
     const int B0 = blocks[bi].first, B1 = blocks[bi].second;
     const int k0 = back ? B1 : 0, k1 = back ? N : B0;  // known entries
     for (int attempt = 0;; attempt++) {
       if (attempt > 6) return HK_ERR_RANGE;
-      long long h, top;
+      long long h, top, lo = 0, hi = 0;
       const bool have_known = k1 > k0;
       if (have_known) {
         // exact exponent range of the known entries (scaled by 2^g_k in the back solve)
@@ -931,7 +1125,8 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
         long long hh[2];
         CK(cudaMemcpyAsync(hh, c->d_range, sizeof(hh), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
-        long long lo = hh[0], hi = hh[1];
+        lo = hh[0];
+        hi = hh[1];
         if (lo == LLONG_MAX) {  // all known entries are zero
           lo = 0;
           hi = P;
@@ -942,117 +1137,112 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
         h = 0;
         top = 4 * 32;
       }
-      sp.nosum = have_known ? 0 : 1;
-      // Karatsuba on the factor's split points when the vector fits the
-      // factor's window W: the block's GEMV contracts the expanded R entries
-      // with the known vector entries, expanded for this block's grid in one
-      // parallel launch.  The in-block updates (one new entry at a time) use
-      // the plain aligned operands, so no expansion sits on the per-entry chain.
-      const int Wv_need = std::max(4, round4((top - h + 31) / 32));
-      const bool kar_ok = c->fac_levels > 0 && c->Aexp && c->update_path == 0;
-      const int lv = kar_ok && Wv_need <= W ? c->fac_levels : 0;
-      const int Wv = lv > 0 ? W : Wv_need;
-      if (Wv > HK_MAX_WV) return HK_ERR_RANGE;  // no shared-memory tile could hold it
+      // the prepared GEMV serves this block when its grid holds this block's range
+      const bool use_pf = pf.live && pf.B0 == B0 && have_known && pf.g.h <= h &&
+                          top <= pf.g.h + 32LL * pf.g.Wv;
+      if (pf.live) {
+        // its launches (and status writes) precede everything below
+        CK(cudaEventRecord(c->sv_done, c->la_lo));
+        CK(cudaStreamWaitEvent(c->stream, c->sv_done, 0));
+        pf.live = false;
+        (use_pf ? c->pf_hits : c->pf_miss)++;
+      }
+      SolveGrid g;
+      VecSet vs;
+      if (use_pf) {
+        g = pf.g;
+        vs = pf.vs;
+        cur = pf.set;
+      } else {
+        int rc = solve_grid(c, h, top, &g);
+        if (rc) return rc;
+        rc = ensure_vec(c, g.Wv, g.Cs, nbs, g.lv > 0 ? c->kl.stride : 0);
+        if (rc) return rc;
+        vs = vec_set(c, cur);
+      }
       if (have_known) {
-        c->wv_max = std::max<long long>(c->wv_max, Wv);
-        c->wv_sum += Wv;
+        c->wv_max = std::max<long long>(c->wv_max, g.Wv);
+        c->wv_sum += g.Wv;
         c->wv_count++;
       }
-      Sched sc, sc0;  // GEMV schedule; plain schedule of the in-block updates
-      CK(sched_for(c, W, Wv, lv, &sc));
-      sc0 = sc;
-      if (lv > 0) CK(sched_for(c, W, Wv, 0, &sc0));
-      const int Cs = std::max(sc.C, sc0.C);  // column-sum row width serving both
-      int rc = ensure_vec(c, Wv, Cs, nbs, lv > 0 ? c->kl.stride : 0);
-      if (rc) return rc;
+      // prepare the next block's GEMV against the entries known now
+      const bool prep = la && have_known && bi + 1 < blocks.size();
+      SolveGrid gn;
+      VecSet vn;
+      if (prep) {
+        // the next block's range: this one's, widened by twice the growth
+        // the last block brought (at least 64 bits on each side)
+        const long long lo_n = lo - 2 * std::max(grow_lo, 64LL);
+        const long long hi_n = hi + 2 * std::max(grow_hi, 64LL);
+        long long hn = lo_n - margin, topn = hi_n + margin;
+        int rc = solve_grid(c, hn, topn, &gn);
+        if (rc) return rc;
+        if (gn.lv > 0) gn.h -= (32LL * gn.Wv - (topn - hn)) / 2;  // centre the spare room of the window
+        rc = ensure_vec(c, std::max(g.Wv, gn.Wv), std::max(g.Cs, gn.Cs), nbs,
+                        (g.lv > 0 || gn.lv > 0) ? c->kl.stride : 0);
+        if (rc) return rc;
+        if (!use_pf) vs = vec_set(c, cur);  // a growth replaced the buffers (the old ones stay allocated)
+        vn = vec_set(c, 1 - cur);
+      }
+      if (!use_pf)
+        CK(cudaMemsetAsync(vs.colsum, 0, sizeof(long long) * (size_t)(B1 - B0) * g.Cs, c->stream));
+      if (prep) {
+        const int nB0 = blocks[bi + 1].first, nB1 = blocks[bi + 1].second;
+        CK(cudaEventRecord(c->sv_fork, c->stream));
+        CK(cudaStreamWaitEvent(c->la_lo, c->sv_fork, 0));
+        CK(cudaMemsetAsync(vn.colsum, 0, sizeof(long long) * (size_t)(nB1 - nB0) * gn.Cs, c->la_lo));
+        int rc = solve_gemv(c, gn, vn, out, back, nB0, nB1, k0, k1, c->la_lo);
+        if (rc) return rc;
+      }
+      ev_begin(c, 2);
+      if (use_pf) {
+        // only the entries the prepared GEMV has not seen: the last block's
+        const int na = pf.t0 == k0 ? pf.t1 : k0, nb = pf.t0 == k0 ? k1 : pf.t0;
+        int rc = solve_gemv(c, g, vs, out, back, B0, B1, na, nb, c->stream);
+        if (rc) return rc;
+      } else if (have_known) {
+        int rc = solve_gemv(c, g, vs, out, back, B0, B1, k0, k1, c->stream);
+        if (rc) return rc;
+      }
+      if (prep) {
+        pf.live = true;
+        pf.B0 = blocks[bi + 1].first;
+        pf.t0 = k0;
+        pf.t1 = k1;
+        pf.set = 1 - cur;
+        pf.g = gn;
+        pf.vs = vn;
+      }
       sp.kl = c->kl;
       sp.kl.levels = 0;  // solve entries write only their aligned form
-      sp.vecAexp = c->vecAexp;
-      sp.vecA = c->vecA;
-      sp.vecAsign = c->vecAsign;
-      sp.Wv = Wv;
-      sp.C = Cs;
-      sp.h = h;
-      sp.colsum = c->colsum_s;
-      sp.colsum_len = (long long)c->colsum_s_cap;
-      sp.vec_len = (long long)c->vec_cap;
+      sp.vecAexp = vs.Aexp;
+      sp.vecA = vs.A;
+      sp.vecAsign = vs.sign;
+      sp.Wv = g.Wv;
+      sp.C = g.Cs;
+      sp.h = g.h;
+      sp.colsum = vs.colsum;
+      sp.colsum_len = vs.colsum_len;
+      sp.vec_len = vs.A_len;
       sp.r0 = B0;
-      CK(cudaMemsetAsync(c->colsum_s, 0, sizeof(long long) * (size_t)(B1 - B0) * Cs, c->stream));
-      ev_begin(c, 2);
-      if (have_known) {
-        CK(launch_vec_align(k0, k1, out, L, c->colG, back ? 1 : 0, h, Wv, c->vecA, c->vecAsign, c->st,
-                            (long long)c->vec_cap, c->stream));
-        DBG(c, "solve vec_align", B0, Wv);
-        c->launches++;
-        if (lv > 0) {
-          CK(launch_vec_expand(k0, k1, c->vecA, c->kl, c->vecAexp, c->stream));
-          DBG(c, "solve vec_expand", B0, Wv);
-          c->launches++;
-        }
-      }
-      UpdParams up;
-      std::memset(&up, 0, sizeof(up));
-      up.wait_ns = c->wait_ns;
-      up.mode = back ? M_GEMV_BACK : M_GEMV_FWD;
-      up.N = N;
-      up.A = lv > 0 ? c->Aexp : c->A;
-      up.Asign = c->Asign;
-      up.astride = lv > 0 ? c->kl.stride : W;
-      up.Vy = lv > 0 ? c->vecAexp : c->vecA;
-      up.Vysign = c->vecAsign;
-      up.vstride = lv > 0 ? c->kl.stride : Wv;
-      up.cx = up.astride;
-      up.cy = up.vstride;
-      up.r0 = B0;
-      up.colsum = c->colsum_s;
-      up.a_len = lv > 0 ? c->Aexp_len : c->A_len;
-      up.vy_len = lv > 0 ? (long long)c->vecAexp_cap : (long long)c->vec_cap;
-      up.colsum_len = (long long)c->colsum_s_cap;
-      fill_sched(up, sc);
-      up.C = Cs;
-      up.st = c->st;
-      UpdParams upi = up;  // in-block updates
-      if (lv > 0) {
-        upi.A = c->A;
-        upi.astride = W;
-        upi.Vy = c->vecA;
-        upi.vstride = Wv;
-        upi.cx = W;
-        upi.cy = Wv;
-        upi.a_len = c->A_len;
-        upi.vy_len = (long long)c->vec_cap;
-        fill_sched(upi, sc0);
-        upi.C = Cs;
-      }
-      const long long cta_per_out = (sc.n + UNT - 1) / UNT;
-      const long long target = 6LL * sm_count(c) * 3;
-      if (have_known) {
-        up.ra = B0;
-        up.rb = B1;
-        up.nout = B1 - B0;
-        up.t0 = k0;
-        up.t1 = k1;
-        up.tchunk = pick_tchunk(k1 - k0, cta_per_out * (B1 - B0), target);
-        CK(launch_update(up, c->stream));
-        DBG(c, "gemv/dot update", up.ra, up.t0);
-        c->launches++;
-      }
-      sp.h = h;
+      sp.nosum = have_known ? 0 : 1;
+      UpdParams upi = solve_upd(c, g, vs, back, false);  // in-block updates
+      upi.r0 = B0;
       // low precision: the whole block in one launch (its per-row launches
       // would cost more than their work); high precision: entry by entry with
       // many-CTA in-block updates
-      const bool fused = (long long)W * Wv <= c->fuse_ww && Cs >= W + Wv + 4 &&
-                         solve_block_smem(L, Cs, W, Wv, B1 - B0) <= 160 * 1024;
+      const bool fused = (long long)c->W * g.Wv <= c->fuse_ww && g.Cs >= c->W + g.Wv + 4 &&
+                         solve_block_smem(L, g.Cs, c->W, g.Wv, B1 - B0) <= 160 * 1024;
       if (fused) {
         CK(launch_solve_block(sp, c->A, c->Asign, B0, B1, c->stream));
-        DBG(c, "solve block", B0, Wv);
+        DBG(c, "solve block", B0, g.Wv);
         c->launches++;
       }
       for (int s = 0; s < B1 - B0 && !fused; s++) {
         const int i = back ? B1 - 1 - s : B0 + s;
         // the first entry of each solve has no sum: the kernel takes G from the rhs
         CK(launch_solve_entry(sp, i, c->stream));
-        DBG(c, "solve entry", i, Wv);
+        DBG(c, "solve entry", i, g.Wv);
         c->launches++;
         const bool more = back ? (i > B0) : (i + 1 < B1);
         if (more) {
@@ -1078,6 +1268,12 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
       if (st.timeout) return HK_ERR_TIMEOUT;
       if (st.range_fail) {
         margin = margin * 4 + st.need_bits;
+        if (pf.live) {
+          // the prepared GEMV used the old margin: wait for it and drop it
+          CK(cudaStreamSynchronize(c->la_lo));
+          pf.live = false;
+          c->pf_miss++;
+        }
         CK(reset_status(c));
         continue;
       }
@@ -1086,6 +1282,14 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
         fprintf(stderr, "[hk checked] solve block %d status code %d check_site %d\n", B0, st.code, st.check_site);
 #endif
         return st.code == ST_NOT_PD ? HK_ERR_NOT_PD : HK_ERR_CUDA;
+      }
+      if (have_known) {
+        if (prev_lo != LLONG_MAX) {
+          grow_lo = prev_lo - lo;
+          grow_hi = hi - prev_hi;
+        }
+        prev_lo = lo;
+        prev_hi = hi;
       }
       break;
     }
@@ -1239,6 +1443,8 @@ void hk_destroy(hk_ctx *c) {
   if (c->la_hi) cudaStreamDestroy(c->la_hi);
   if (c->la_lo) cudaStreamDestroy(c->la_lo);
   for (cudaEvent_t e : c->la_ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : {c->sv_fork, c->sv_done, c->sv_join})
+    if (e) cudaEventDestroy(e);
   c->sol_arena.release();
   c->fac_arena.release();
   c->res_arena.release();
@@ -1274,10 +1480,12 @@ int hk_workspace_bytes(int N, int P, size_t *bytes) {
   b += NT * (4 * W + 4);                  // aligned R
   b += NT * 4LL * kstride;                // its Karatsuba expansion
   b += (long long)N * recip_limbs((int)L) * 4;  // reciprocals
-  b += 16LL * N * C * 8;                  // column sums of one block
+  b += 2LL * 16 * N * C * 8;              // column sums of two blocks (lookahead)
   b += 3LL * N * (16 + 4 * L) + 256LL * (16 + 4 * L);  // v, y, w, history
   const long long Wv = 2 * W + (long long)N;  // vector window (generous)
-  b += 2LL * N * (4 * Wv + 4) * 5 / 4 + 16LL * (W + Wv + 64) * 8 * 5 / 4;
+  // solves: three aligned vectors (two sets of the lookahead and the Rayleigh
+  // quotient's second operand), two Karatsuba expansions, two column-sum blocks
+  b += 3LL * N * (4 * Wv + 4) * 5 / 4 + 2LL * N * 4 * kstride + 2LL * 16 * (W + Wv + 64) * 8 * 5 / 4;
   b += 8LL << 20;                         // unit tables, alignment slack
   *bytes = (size_t)b * 2;                 // two widenings of slack for the bump allocator
   return HK_OK;
@@ -1300,6 +1508,7 @@ int hk_set_workspace(hk_ctx *c, void *dev_ptr, size_t bytes) {
   c->loaded = c->factored = c->sol_ready = false;
   c->hist_cap = 0;
   c->vec_cap = 0;
+  c->vecAexp_cap = 0;
   c->colsum_s_cap = 0;
   c->fac_N = c->fac_L = c->fac_W = 0;
   c->mom = MpArr{};
@@ -1595,6 +1804,7 @@ int hk_smallest_eig(hk_ctx *c, int iters, hk_mp *lambda_min, int *iters_used) {
   if (const char *e = getenv("HK_SOLVE_MARGIN")) c->solve_margin = std::max(32LL, atoll(e));  // (tuning)
   c->eig_converged = 0;
   c->wv_max = c->wv_sum = c->wv_count = 0;
+  c->pf_hits = c->pf_miss = 0;
   int rc = ensure_solve_buffers(c, T);
   if (rc) return rc;
   c->t_phase[2] = 0;
@@ -1701,7 +1911,7 @@ int hk_get_stats(hk_ctx *c, int64_t *out, int n) {
   const int ns = kar_subprobs(kl, sub);
   int64_t per_mac = 0;
   for (int k = 0; k < ns; k++) per_mac += (int64_t)sub[k].wx * sub[k].wy;
-  const int64_t v[9] = {c->launches,
+  const int64_t v[11] = {c->launches,
                         c->W,
                         c->widenings,
                         lv,
@@ -1709,9 +1919,11 @@ int hk_get_stats(hk_ctx *c, int64_t *out, int n) {
                         c->eig_converged,
                         c->wv_max,
                         c->wv_count ? c->wv_sum / c->wv_count : 0,
-                        c->resumes};
-  for (int k = 0; k < n && k < 9; k++) out[k] = v[k];
-  for (int k = 9; k < n; k++) out[k] = 0;
+                        c->resumes,
+                        c->pf_hits,
+                        c->pf_miss};
+  for (int k = 0; k < n && k < 11; k++) out[k] = v[k];
+  for (int k = 11; k < n; k++) out[k] = 0;
   return HK_OK;
 }
 
@@ -1734,12 +1946,11 @@ int hk_update_plan(int W, int levels, int64_t *info, int32_t *splits, int32_t *p
   std::vector<Unit> h;
   plan_units(sp, W, W, lv, uc, upc, &sc, &h);
   if (units && ucap < sc.n) return HK_ERR_ARG;
-  const int64_t v[9] = {lv, sc.nsub, lv > 0 ? sp.kl.stride : W, lv > 0 ? sp.kl.G : 0, uc, upc, sc.n, sc.nxb, sc.C};
+  const int64_t v[9] = {lv > 0 ? sp.kl.levels : 0, sc.nsub, lv > 0 ? sp.kl.stride : W, lv > 0 ? sp.kl.G : 0,
+                        uc, upc, sc.n, sc.nxb, sc.C};
   for (int k = 0; k < 9; k++) info[k] = v[k];
   if (splits) {
-    splits[0] = sp.kl.m1;
-    for (int k = 0; k < 3; k++) splits[1 + k] = sp.kl.m2[k];
-    for (int k = 0; k < 9; k++) splits[4 + k] = sp.kl.m3[k];
+    for (int k = 0; k < MAX_SPLITS; k++) splits[k] = sp.kl.ms[k];
   }
   for (int k = 0; k < sc.nsub; k++) {
     if (pieces) {

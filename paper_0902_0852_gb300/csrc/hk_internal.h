@@ -21,9 +21,16 @@ constexpr int UPC = 36;        // default p-steps per unit (a multiple of the st
 constexpr int UNT = 256;       // compute threads per CTA
 constexpr int USTAGES = 4;     // default shared-memory pipeline depth
 constexpr int USTAGES_MAX = 8; // deepest ring a launch may use
-constexpr int MAX_KAR = 3;     // Karatsuba levels of the expansion
-constexpr int MAX_SUB = 27;    // sub-contractions per launch (3^levels)
-constexpr int MAX_TERMS = 8;   // result positions a sub-contraction is added to (2^levels)
+constexpr int MAX_KAR = 4;     // Karatsuba levels of the expansion
+constexpr int MAX_SUB = 81;    // sub-contractions per launch (3^levels)
+constexpr int MAX_TERMS = 16;  // result positions a sub-contraction is added to (2^levels)
+constexpr int MAX_SPLITS = 40; // split points of all levels (1 + 3 + 9 + 27)
+// first split of level lv (1-based) in KarLayout::ms: (3^(lv-1) - 1) / 2
+__host__ __device__ inline int split_base(int lv) {
+  int b = 0, n = 1;
+  for (int l = 1; l < lv; l++, n *= 3) b += n;
+  return b;
+}
 constexpr int MAX_XB = 64;     // blocks per output with their own operand window
 // Guard bits of the stored row reciprocals floor(2^(2P+1+RECIP_EXTRA)/mant(R_ii)):
 // with them a correctly rounded division rarely needs its exact remainder.
@@ -49,7 +56,7 @@ struct SubProb {
   int tsign[MAX_TERMS];
 };
 
-// Karatsuba expansion of an aligned entry of W limbs (levels 0 to 3):
+// Karatsuba expansion of an aligned entry of W limbs (levels 0 to 4):
 // pieces lo, hi, lo+hi (recursively), each stored in its own slot with zero
 // gaps of G limbs on both sides, so that one entry is one contiguous copy.
 // Piece k of the last level is the base-3 path (lo = 0, hi = 1, lo+hi = 2)
@@ -58,9 +65,7 @@ struct KarLayout {
   int levels;
   int W;
   int npieces;
-  int m1;                  // level-1 split
-  int m2[3];               // level-2 splits of lo, hi, lo+hi
-  int m3[9];               // level-3 splits of the nine level-2 pieces
+  int ms[MAX_SPLITS];      // split points: level lv's piece u splits at ms[split_base(lv) + u]
   int off[MAX_SUB];        // slot offsets (limbs)
   int w[MAX_SUB];          // piece widths
   int G;                   // gap (limbs)
@@ -84,7 +89,7 @@ struct UpdParams {
   int uc;                  // stripe width of the unit table (7, 9, 11 or 13)
   int upc;                 // p-steps per unit (a multiple of uc)
   int nsub;
-  SubProb sub[MAX_SUB];
+  const SubProb *sub;      // [nsub] sub-contractions (device memory)
   int r0;                  // first row of the current block (output indexing)
   int ra, rb;              // output rows [ra, rb)
   int nout;                // number of outputs

@@ -13,7 +13,7 @@
 //   sum a_i a_j = C0 + B (Cs - C0 - C1) + B^2 C1,
 //   C0 = sum a0_i a0_j, C1 = sum a1_i a1_j, Cs = sum (a0+a1)_i (a0+a1)_j,
 // so one launch runs a list of smaller contractions ("sub-problems", 3^levels
-// for up to three levels), each added to the column sums at its (offset, sign)
+// for up to four levels), each added to the column sums at its (offset, sign)
 // terms (up to 2^levels of them).
 // The identity is exact, so results do not depend on the expansion depth.
 //
@@ -474,6 +474,7 @@ cudaError_t allow_dynamic_smem(const void *fn) {
 void kar_layout(int W, int levels, int gap, KarLayout *kl) {
   KarLayout k{};
   levels = std::max(0, std::min(levels, MAX_KAR));
+  if (W < 64) levels = std::min(levels, 3);  // the expansion's temporaries need W >= 64 at four levels
   k.levels = levels;
   k.W = W;
   k.G = ((gap + 3) / 4) * 4;
@@ -484,9 +485,7 @@ void kar_layout(int W, int levels, int gap, KarLayout *kl) {
     std::vector<int> nw;
     for (size_t u = 0; u < w.size(); u++) {
       const int m = (w[u] + 1) / 2;
-      if (lv == 1) k.m1 = m;
-      if (lv == 2) k.m2[u] = m;
-      if (lv == 3) k.m3[u] = m;
+      k.ms[split_base(lv) + (int)u] = m;
       nw.push_back(m);
       nw.push_back(w[u] - m);
       nw.push_back(std::max(m, w[u] - m) + 1);
@@ -552,7 +551,7 @@ int kar_subprobs(const KarLayout &kl, SubProb *sub) {
       int div = 1;
       for (int r = lv; r < kl.levels; r++) div *= 3;
       const int digit = (i / div) % 3;
-      const int m = lv == 1 ? kl.m1 : (lv == 2 ? kl.m2[parent] : kl.m3[parent]);
+      const int m = kl.ms[split_base(lv) + parent];
       int o[2], sg[2];
       const int nc = coef(digit, m, o, sg);
       int toff[MAX_TERMS], tsign[MAX_TERMS], n = 0;
@@ -728,11 +727,15 @@ void choose_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc_out, int
 // Karatsuba depth for a window of W limbs: the level count whose best
 // schedule has the least modelled cost (the model of choose_schedule, which
 // counts every thread slot of the unit grid, so narrow pieces pay for their
-// idle slots and per-unit overhead).
+// idle slots and per-unit overhead), up to MAX_AUTO_KAR levels.  The model
+// does not see the staged operand windows, which grow with the zero gaps of
+// 81 pieces (at W = 300 a four-level block would stage about 114 KB, one
+// block per SM); deeper expansions are taken by option only.
+constexpr int MAX_AUTO_KAR = 3;
 int choose_levels(int W, int gap) {
   int best_lv = 0;
   double best = 1e300;
-  for (int lv = 0; lv <= MAX_KAR; lv++) {
+  for (int lv = 0; lv <= MAX_AUTO_KAR; lv++) {
     KarLayout kl;
     kar_layout(W, lv, gap, &kl);
     SubProb sub[MAX_SUB];
@@ -791,7 +794,7 @@ cudaError_t launch_wait_selftest(DevStatus *st, long long wait_ns, cudaStream_t 
 
 cudaError_t launch_update(const UpdParams &p, cudaStream_t s) {
   if (p.nout <= 0 || p.t1 <= p.t0 || p.nunits <= 0) return cudaSuccess;
-  if (p.upc % p.uc != 0 || p.nsub < 1 || p.nsub > MAX_SUB) return cudaErrorInvalidValue;
+  if (p.upc % p.uc != 0 || p.nsub < 1 || p.nsub > MAX_SUB || !p.sub) return cudaErrorInvalidValue;
   switch (p.uc) {
     case 7: return launch_uc<7>(p, s);
     case 8: return launch_uc<8>(p, s);

@@ -254,11 +254,11 @@ def hk_get_timings(ctx):
 
 
 def hk_get_stats(ctx):
-    out = (ctypes.c_int64 * 9)()
-    _check(lib().hk_get_stats(ctx, out, 9), "hk_get_stats")
+    out = (ctypes.c_int64 * 11)()
+    _check(lib().hk_get_stats(ctx, out, 11), "hk_get_stats")
     return {"launches": out[0], "W": out[1], "widenings": out[2], "karatsuba_levels": out[3],
             "limbprod_per_mac": out[4], "converged": out[5], "solve_wv_max": out[6], "solve_wv_mean": out[7],
-            "resumes": out[8]}
+            "resumes": out[8], "solve_prepared_used": out[9], "solve_prepared_dropped": out[10]}
 
 
 def hk_selftest_mp(op, L, x, ex=0, y=None, ey=0):
@@ -558,9 +558,9 @@ def hk_update_plan(W, levels=-1, with_units=True):
     per-block operand windows -- what hk_factor launches for that window."""
     L = lib()
     info = (ctypes.c_int64 * 9)()
-    splits = (ctypes.c_int32 * 13)()
-    pieces = (ctypes.c_int32 * (3 * 27))()
-    terms = (ctypes.c_int32 * (2 * 8 * 27))()
+    splits = (ctypes.c_int32 * 40)()
+    pieces = (ctypes.c_int32 * (3 * 81))()
+    terms = (ctypes.c_int32 * (2 * 16 * 81))()
     _check(L.hk_update_plan(W, levels, info, splits, pieces, terms, None, 0, None), "hk_update_plan")
     n, nunits, nxb = info[1], info[6], info[7]
     units = win = None
@@ -581,9 +581,9 @@ def hk_update_plan(W, levels=-1, with_units=True):
     return {
         "levels": info[0], "npieces": n, "stride": info[2], "gap": info[3], "uc": info[4], "upc": info[5],
         "nunits": nunits, "nxb": nxb, "C": info[8],
-        "m1": splits[0], "m2": list(splits[1:4]), "m3": list(splits[4:13]),
+        "m1": splits[0], "m2": list(splits[1:4]), "m3": list(splits[4:13]), "m4": list(splits[13:40]),
         "pieces": [(pieces[3 * k], pieces[3 * k + 1]) for k in range(n)],
-        "terms": [[(terms[2 * (8 * k + t)], terms[2 * (8 * k + t) + 1]) for t in range(pieces[3 * k + 2])]
+        "terms": [[(terms[2 * (16 * k + t)], terms[2 * (16 * k + t) + 1]) for t in range(pieces[3 * k + 2])]
                   for k in range(n)],
         "units": units, "windows": win,
     }

@@ -12,7 +12,7 @@ int main(void) {
   if (hk_workspace_bytes(10, 48, &bytes) != HK_ERR_ARG) return 2;
   if (strcmp(hk_strerror(HK_OK), "ok") != 0) return 3;
   int64_t info[9];
-  int32_t splits[13], pieces[3 * 27], terms[2 * 8 * 27];
+  int32_t splits[40], pieces[3 * 81], terms[2 * 16 * 81];
   if (hk_update_plan(804, -1, info, splits, pieces, terms, NULL, 0, NULL) != HK_OK) return 4;
   if (info[0] < 0 || info[0] > 3 || info[1] < 1 || info[6] < 1) return 5;
   if (hk_factor(NULL, NULL) != HK_ERR_ARG || hk_smallest_eig(NULL, 1, NULL, NULL) != HK_ERR_ARG) return 6;

@@ -205,8 +205,8 @@ def test_solve_paths_bit_identical(hk, monkeypatch, fuse):
 
 @pytest.mark.parametrize("N,beta,P", [(40, (7, 4), 2048), (24, (3, 4), 8192)])
 def test_karatsuba_depths_bit_identical(hk, N, beta, P):
-    """The factor update contracts Karatsuba pieces of one to three levels (27
-    sub-contractions at three, each added at up to eight offsets); the
+    """The factor update contracts Karatsuba pieces of one to four levels (81
+    sub-contractions at four, each added at up to sixteen offsets); the
     identity is exact, so R and the inverse-iteration history (whose solves
     expand the vector with the same split points) equal the oracle's at every
     depth, and the automatic choice (-1) is one of them."""
@@ -214,7 +214,7 @@ def test_karatsuba_depths_bit_identical(hk, N, beta, P):
     Ro = oracle.cholesky(m, N, P)
     _, hist_o, _ = oracle.inverse_iteration(Ro, P, 4)
     seen = set()
-    for lv in (-1, 0, 1, 2, 3):
+    for lv in (-1, 0, 1, 2, 3, 4):
         with hk.Hankel(0) as h:
             h.set_option(hk.HK_OPT_KARATSUBA, lv)
             h.load(N, beta, P, m)
@@ -228,7 +228,7 @@ def test_karatsuba_depths_bit_identical(hk, N, beta, P):
         if lv >= 0:
             assert st["karatsuba_levels"] == lv
         seen.add(st["karatsuba_levels"])
-    assert len(seen) == 4
+    assert len(seen) == 5
 
 
 @pytest.mark.parametrize("N,beta,P,nb", [(100, (7, 4), 1024, 16), (90, (1, 1), 768, 8), (64, (3, 4), 2048, 16)])
@@ -250,8 +250,38 @@ def test_lookahead_bit_identical(hk, N, beta, P, nb):
             R = h.R()
             lam, used = h.smallest_eig(3)
             hist = h.history(3)
+            st = h.stats()
         assert R == Ro, (la, graph)
         assert hist == hist_o, (la, graph)
+        if la:
+            # the solves' prepared GEMVs were used (and any dropped ones fell back)
+            assert st["solve_prepared_used"] > 0, st
+        else:
+            assert st["solve_prepared_used"] == 0 and st["solve_prepared_dropped"] == 0, st
+
+
+@pytest.mark.parametrize("N,beta,P,fuse,margin", [(120, (7, 4), 1024, "0", "32"), (100, (1, 1), 640, None, "32"),
+                                                  (96, (3, 4), 1536, "0", "4096")])
+def test_solve_lookahead_fallbacks_bit_identical(hk, monkeypatch, N, beta, P, fuse, margin):
+    """Solve lookahead under stress: the narrowest first-attempt margin (the
+    block ranges outgrow it, so blocks retry with a wider one and drop the GEMV
+    prepared for the next block) and a wide one, per-entry and fused block
+    solves.  The inverse-iteration history equals the oracle's bit for bit."""
+    if fuse is not None:
+        monkeypatch.setenv("HK_FUSE_WW", fuse)
+    monkeypatch.setenv("HK_SOLVE_MARGIN", margin)
+    m = inputs.moments(N, beta, P)
+    Ro = oracle.cholesky(m, N, P)
+    _, hist_o, _ = oracle.inverse_iteration(Ro, P, 3)
+    with hk.Hankel(0) as h:
+        h.set_option(hk.HK_OPT_LOOKAHEAD, 1)
+        h.load(N, beta, P, m)
+        h.factor()
+        lam, used = h.smallest_eig(3)
+        hist = h.history(3)
+        st = h.stats()
+    assert hist == hist_o, st
+    assert st["solve_prepared_used"] + st["solve_prepared_dropped"] > 0, st
 
 
 # Slack 0 fails in the first block (a restart).  L = P/32 = 15 leaves exactly
@@ -304,3 +334,27 @@ def test_sampled_rows_beyond_the_configs(hk):
         h.factor()
         R = h.R()
     assert check_rows(m, R, P, [0, 1, 15, 16, 17, 255, 256, 300, 511], max_cols=64) == []
+
+
+@pytest.mark.parametrize("N,beta,P", [(80, (7, 4), 1024), (130, (1, 1), 768)])
+def test_caller_workspace_bit_identical(hk, N, beta, P):
+    """With a caller-owned workspace of exactly hk_workspace_bytes(N, P) (no
+    library allocations: factor buffers, both solve vector sets of the
+    lookahead, unit tables), R and the history equal the oracle's."""
+    import torch
+    m = inputs.moments(N, beta, P)
+    Ro = oracle.cholesky(m, N, P)
+    _, hist_o, _ = oracle.inverse_iteration(Ro, P, 3)
+    ws = torch.empty(hk.hk_workspace_bytes(N, P), dtype=torch.uint8, device="cuda")
+    with hk.Hankel(0) as h:
+        hk.hk_set_workspace(h.ctx, ws)
+        h.load(N, beta, P, m)
+        h.factor()
+        R = h.R()
+        lam, used = h.smallest_eig(3)
+        hist = h.history(3)
+        st = h.stats()
+    torch.cuda.synchronize()
+    assert R == Ro
+    assert hist == hist_o
+    assert st["solve_prepared_used"] > 0, st

@@ -58,15 +58,27 @@ def test_committed_network_covers_every_training_instance():
 def test_heldout_evaluation_rows_and_summary_agree():
     e = _load("predictor_eval.json")
     rows, s = e["rows"], e["summary"]
-    assert s["instances"] == len(rows)
+    assert s["instances"] == len(rows) == 256
+    both = [r for r in rows if "cons_seconds" in r]
+    assert s["conservative_checked"] == len(both) >= len(rows) // 4
     for r in rows:
         assert 513 <= r["N"] <= 800
-        assert r["verified"] and r["agree_bits"] >= pr.AGREE_BITS
-        assert r["tried"][0] == r["P_pred"] and r["P_pred"] < r["P_cons"]
+        P_cons = pr.p_conservative(r["N"], tuple(r["beta"]))
+        assert r["verified"]
+        assert r["tried"][0] == r["P_pred"] and r["P_pred"] < P_cons
+    for r in both:
         assert r["P_cons"] == pr.p_conservative(r["N"], tuple(r["beta"]))
+        assert r["agree_bits"] >= pr.AGREE_BITS  # verified value = conservative value to 2^-128
     assert s["all_verified"] == all(r["verified"] for r in rows)
-    assert abs(s["conservative_seconds"] - sum(r["cons_seconds"] for r in rows)) < 1e-2
-    assert abs(s["predicted_seconds"] - sum(r["pred_seconds"] for r in rows)) < 1e-2
-    assert abs(s["gain"] - s["conservative_seconds"] / s["predicted_seconds"]) < 1e-3
+    assert abs(s["conservative_seconds"] - sum(r["cons_seconds"] for r in both)) < 1e-2
+    assert abs(s["predicted_seconds_same_instances"] - sum(r["pred_seconds"] for r in both)) < 1e-2
+    assert abs(s["predicted_seconds_all"] - sum(r["pred_seconds"] for r in rows)) < 1e-2
+    assert abs(s["gain"] - s["conservative_seconds"] / s["predicted_seconds_same_instances"]) < 1e-3
     assert s["escalated"] == sum(1 for r in rows if len(r["tried"]) > 2)
-    assert abs(s["min_agree_bits"] - min(r["agree_bits"] for r in rows)) < 1e-6
+    assert abs(s["min_agree_bits"] - min(r["agree_bits"] for r in both)) < 1e-6
+
+
+def test_training_set_size():
+    """4096 training instances (seed 1), at least 90% of them with a tuple."""
+    d = _load("predictor_tuples.json")
+    assert d["meta"]["count"] == 4096 and len(d["tuples"]) == 4096

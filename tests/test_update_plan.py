@@ -24,7 +24,7 @@ def expand(a, W, plan):
     """Pieces of a (W limbs) in slot order: each level splits every piece of
     width w at the plan's split point into lo, hi and lo + hi."""
     cur = [(a, W)]
-    splits = [[plan["m1"]], plan["m2"], plan["m3"]]
+    splits = [[plan["m1"]], plan["m2"], plan["m3"], plan["m4"]]
     for lv in range(plan["levels"]):
         nxt = []
         for u, (x, w) in enumerate(cur):
@@ -36,10 +36,12 @@ def expand(a, W, plan):
     return cur
 
 
-@pytest.mark.parametrize("W", [5, 13, 41, 176, 400, 804])
-@pytest.mark.parametrize("levels", [0, 1, 2, 3])
+@pytest.mark.parametrize("W", [5, 13, 41, 64, 176, 400, 804])
+@pytest.mark.parametrize("levels", [0, 1, 2, 3, 4])
 def test_karatsuba_terms_reproduce_the_product(hk, W, levels):
     plan = hk.hk_update_plan(W, levels, with_units=False)
+    if W < 64:
+        levels = min(levels, 3)  # four levels need a window of at least 64 limbs
     assert plan["levels"] == levels and plan["npieces"] == 3 ** levels
     rng = random.Random(W * 10 + levels)
     for trial in range(6):
@@ -60,7 +62,7 @@ def test_karatsuba_terms_reproduce_the_product(hk, W, levels):
 
 
 @pytest.mark.parametrize("W", [13, 176, 804])
-@pytest.mark.parametrize("levels", [1, 2, 3])
+@pytest.mark.parametrize("levels", [1, 2, 3, 4])
 def test_piece_slots_are_separated_by_zero_gaps(hk, W, levels):
     plan = hk.hk_update_plan(W, levels, with_units=False)
     G = plan["gap"]
@@ -72,7 +74,7 @@ def test_piece_slots_are_separated_by_zero_gaps(hk, W, levels):
 
 
 def _plans():
-    return [(176, -1), (400, -1), (804, -1), (804, 2), (300, 0)]
+    return [(176, -1), (400, -1), (804, -1), (804, 2), (300, 0), (804, 4), (300, 4)]
 
 
 @pytest.mark.parametrize("W,levels", _plans())
@@ -127,11 +129,11 @@ def test_automatic_depth_follows_the_cost_model(hk):
     assert depths == sorted(depths) and depths[0] == 0
     for W in (8, 64, 176, 804, 1200):
         plan = hk.hk_update_plan(W, -1, with_units=False)
-        assert 0 <= plan["levels"] <= 3 and plan["C"] >= 2 * W
+        assert 0 <= plan["levels"] <= 3 and plan["C"] >= 2 * W  # four levels by option only
 
 
 def test_plan_argument_checks(hk):
     from paper_0902_0852_gb300.hk import HKError
-    for W, lv in [(0, -1), (100, 4), (100, -2)]:
+    for W, lv in [(0, -1), (100, 5), (100, -2)]:
         with pytest.raises(HKError):
             hk.hk_update_plan(W, lv, with_units=False)
