@@ -55,10 +55,10 @@ struct EvPair {
 // unit table and schedule of the update kernel for one operand shape
 struct Sched {
   Unit *units;
-  SubProb *dsub;  // device copy of sub
   int n, uc, upc;
   int nsub;
   SubProb sub[MAX_SUB];
+  KSub ksub[MAX_SUB];  // the kernel's packed copy
   int C;  // column sums per output
   int nxb, maxlen;  // per-block operand windows (Karatsuba), see UpdParams
   int xlo[MAX_XB], xlen[MAX_XB];
@@ -124,6 +124,7 @@ struct hk_ctx {
   int32_t *vecA2sign = nullptr;
   long long *colsum_s2 = nullptr;
   long long pf_hits = 0, pf_miss = 0;  // prepared GEMVs used / dropped in the last eig
+  long long pf_ctas = 0;  // blocks per prepared GEMV launch (0: as the block's own GEMV)
   uint32_t *vecAexp = nullptr;  // Karatsuba expansion of vecA (solves on the factor's window)
   size_t vecAexp_cap = 0;       // limbs
   int32_t *vecAsign = nullptr, *vecBsign = nullptr;
@@ -313,7 +314,6 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
   long long *cs = nullptr;
   DevStatus *st = nullptr;
   Unit *units = nullptr;
-  SubProb *dsub = nullptr;
   const int C = colsum_width(sub, nsub, 7) + 64;
   long long nout = 0;
   for (int i = r0; i < r1; i++) nout += Nt - i;
@@ -321,9 +321,6 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
             cudaMalloc(&cs, (size_t)nout * C * 8 * 2) == cudaSuccess && cudaMalloc(&st, sizeof(DevStatus)) == cudaSuccess;
   const int cap = build_units(sub, nsub, 7, 14, nullptr, 0) + 16;  // the most units of any candidate
   ok = ok && cudaMalloc(&units, (size_t)cap * sizeof(Unit)) == cudaSuccess;
-  ok = ok && cudaMalloc(&dsub, (size_t)nsub * sizeof(SubProb)) == cudaSuccess;
-  ok = ok && cudaMemcpyAsync(dsub, sub, (size_t)nsub * sizeof(SubProb), cudaMemcpyHostToDevice, c->stream) ==
-                 cudaSuccess;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ok) {
     k_fill_random<<<256, 256, 0, c->stream>>>(A, NTt * stride, 12345u);
@@ -356,7 +353,7 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
       up.uc = uc;
       up.upc = upc;
       up.nsub = nsub;
-      up.sub = dsub;
+      for (int k = 0; k < nsub; k++) ok = ok && pack_ksub(sub[k], &up.sub[k]);
       up.r0 = r0;
       up.ra = r0;
       up.rb = r1;
@@ -395,7 +392,6 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
   cudaFree(cs);
   cudaFree(st);
   cudaFree(units);
-  cudaFree(dsub);
   return ok && best < 1e30f;
 }
 
@@ -485,10 +481,8 @@ cudaError_t sched_for(hk_ctx *c, int Wx, int Wy, int levels, Sched *out) {
   plan_units(sp, Wx, Wy, levels, uc, upc, &sc, &h);
   cudaError_t e = alloc(c, c->base_arena, &sc.units, (size_t)sc.n);
   if (e != cudaSuccess) return e;
-  e = alloc(c, c->base_arena, &sc.dsub, (size_t)sc.nsub);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(sc.dsub, sc.sub, sizeof(SubProb) * sc.nsub, cudaMemcpyHostToDevice, c->stream);
-  if (e != cudaSuccess) return e;
+  for (int k = 0; k < sc.nsub; k++)
+    if (!pack_ksub(sc.sub[k], &sc.ksub[k])) return cudaErrorInvalidValue;  // offsets beyond the packed range
   // on the context's stream: a plain cudaMemcpy runs on the legacy default
   // stream, which a non-blocking context stream does not wait for, and for
   // pageable memory it returns before the transfer has landed
@@ -505,7 +499,7 @@ void fill_sched(UpdParams &up, const Sched &sc) {
   up.uc = sc.uc;
   up.upc = sc.upc;
   up.nsub = sc.nsub;
-  up.sub = sc.dsub;
+  for (int k = 0; k < sc.nsub; k++) up.sub[k] = sc.ksub[k];
   up.C = sc.C;
   up.nxb = sc.nxb;
   for (int k = 0; k < sc.nxb; k++) {
@@ -1003,7 +997,7 @@ UpdParams solve_upd(hk_ctx *c, const SolveGrid &g, const VecSet &vs, bool back, 
 // [t0, t1): align those entries to the grid (and expand them), then contract.
 // The column sums accumulate (the caller zeroes them once per block).
 int solve_gemv(hk_ctx *c, const SolveGrid &g, const VecSet &vs, MpArr out, bool back, int B0, int B1, int t0,
-               int t1, cudaStream_t s) {
+               int t1, long long target, cudaStream_t s) {
   if (t1 <= t0) return HK_OK;
   CK(launch_vec_align(t0, t1, out, c->L, c->colG, back ? 1 : 0, g.h, g.Wv, vs.A, vs.sign, c->st, vs.A_len, s));
   DBG(c, "solve vec_align", B0, g.Wv);
@@ -1021,7 +1015,7 @@ int solve_gemv(hk_ctx *c, const SolveGrid &g, const VecSet &vs, MpArr out, bool 
   up.nout = B1 - B0;
   up.t0 = t0;
   up.t1 = t1;
-  up.tchunk = pick_tchunk(t1 - t0, cta_per_out * (B1 - B0), 6LL * sm_count(c) * 3);
+  up.tchunk = pick_tchunk(t1 - t0, cta_per_out * (B1 - B0), target);
   CK(launch_update(up, s));
   DBG(c, "gemv/dot update", up.ra, up.t0);
   c->launches++;
@@ -1191,17 +1185,18 @@ int solve(hk_ctx *c, MpArr rhs, MpArr out, bool back) {
         CK(cudaEventRecord(c->sv_fork, c->stream));
         CK(cudaStreamWaitEvent(c->la_lo, c->sv_fork, 0));
         CK(cudaMemsetAsync(vn.colsum, 0, sizeof(long long) * (size_t)(nB1 - nB0) * gn.Cs, c->la_lo));
-        int rc = solve_gemv(c, gn, vn, out, back, nB0, nB1, k0, k1, c->la_lo);
+        int rc = solve_gemv(c, gn, vn, out, back, nB0, nB1, k0, k1,
+                            c->pf_ctas > 0 ? c->pf_ctas : 6LL * sm_count(c) * 3, c->la_lo);
         if (rc) return rc;
       }
       ev_begin(c, 2);
       if (use_pf) {
         // only the entries the prepared GEMV has not seen: the last block's
         const int na = pf.t0 == k0 ? pf.t1 : k0, nb = pf.t0 == k0 ? k1 : pf.t0;
-        int rc = solve_gemv(c, g, vs, out, back, B0, B1, na, nb, c->stream);
+        int rc = solve_gemv(c, g, vs, out, back, B0, B1, na, nb, 6LL * sm_count(c) * 3, c->stream);
         if (rc) return rc;
       } else if (have_known) {
-        int rc = solve_gemv(c, g, vs, out, back, B0, B1, k0, k1, c->stream);
+        int rc = solve_gemv(c, g, vs, out, back, B0, B1, k0, k1, 6LL * sm_count(c) * 3, c->stream);
         if (rc) return rc;
       }
       if (prep) {
@@ -1802,6 +1797,7 @@ int hk_smallest_eig(hk_ctx *c, int iters, hk_mp *lambda_min, int *iters_used) {
   const int T = iters > 0 ? iters : c->max_iters;
   if (const char *e = getenv("HK_FUSE_WW")) c->fuse_ww = atoll(e);  // (tuning and tests)
   if (const char *e = getenv("HK_SOLVE_MARGIN")) c->solve_margin = std::max(32LL, atoll(e));  // (tuning)
+  if (const char *e = getenv("HK_SOLVE_PF_CTAS")) c->pf_ctas = std::max(0LL, atoll(e));  // (tuning)
   c->eig_converged = 0;
   c->wv_max = c->wv_sum = c->wv_count = 0;
   c->pf_hits = c->pf_miss = 0;

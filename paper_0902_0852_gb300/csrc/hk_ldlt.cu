@@ -127,8 +127,54 @@ __global__ void __launch_bounds__(NT) k_ldl_pivot(LdlParams q, int i) {
   bool xnz = false;  // x = 0 is read from its limbs (an iterate may be zero)
   for (int l = threadIdx.x; l < L; l += NT) xnz |= q.x.limbs[l] != 0;
   const bool xz = q.xzero != 0 || !__syncthreads_or(xnz);
-  const int sgn = form_shifted<NT>(s, colrow, p.C, p.mom.sign[mk], p.mom.exp[mk], p.mom.limbs + (long long)mk * L,
-                                   q.x.sign[0], q.x.exp[0], q.x.limbs, xz, L, 2 * gi, p.st, &nZ, &Gz);
+  const long long G = 2 * gi;  // grid of the diagonal's column sums
+  const uint32_t *mlimbs = p.mom.limbs + (long long)mk * L;
+  int sgn = 0;
+  bool exact = true;
+  if (!xz && q.x.exp[0] + P <= G) {
+    // x lies wholly below the grid (|x| < 2^G).  When the rest of the sum,
+    // Z0 = m_2i - colsum, is at least 2^(G + P + 1) in magnitude, the P-bit
+    // result's ulp is at least 2^(G + 1): every representable value and every
+    // rounding midpoint is a multiple of 2^G, and x moves the exact sum by
+    // less than 2^G, so any stand-in of x's sign and of magnitude below 2^G
+    // gives the same RNE(D_i).  The stand-in 2^(G - 1) costs one bit of grid
+    // where x itself would need the whole gap down to its last bit.
+    sgn = form_shifted<NT>(s, colrow, p.C, p.mom.sign[mk], p.mom.exp[mk], mlimbs, 0, 0, q.x.limbs, true, L, G,
+                           p.st, &nZ, &Gz);
+    if (sgn != 0 && nZ + 1 <= s.cap && mp::bitlen<NT>(s.Z, nZ, *s.red) >= P + 2) {
+      exact = false;
+      // |Z0| 2^G - sign(x) 2^(G-1) = (2|Z0| -+ 1) 2^(G-1), of Z0's sign
+      for (int d = threadIdx.x; d <= nZ; d += NT) {
+        const uint32_t hi = d < nZ ? s.Z[d] : 0u, lo = d >= 1 ? s.Z[d - 1] : 0u;
+        s.tmp[d] = (hi << 1) | (lo >> 31);
+      }
+      __syncthreads();
+      for (int d = threadIdx.x; d <= nZ; d += NT) s.Z[d] = s.tmp[d];
+      __syncthreads();
+      const bool same = (sgn > 0) == (q.x.sign[0] == 0);  // x has Z0's sign: the magnitude shrinks
+      if (!same) {
+        if (threadIdx.x == 0) s.Z[0] |= 1u;  // bit 0 is clear after the shift
+      } else {
+        // subtract one: borrow through the zero limbs below the lowest
+        // nonzero one (the value is at least 2^(P+2), so one exists)
+        __shared__ int low_nz;
+        if (threadIdx.x == 0) low_nz = nZ;
+        __syncthreads();
+        for (int d = threadIdx.x; d <= nZ; d += NT)
+          if (s.Z[d] != 0) atomicMin(&low_nz, d);
+        __syncthreads();
+        const int j = low_nz;
+        for (int d = threadIdx.x; d < j; d += NT) s.Z[d] = 0xffffffffu;
+        if (threadIdx.x == 0) s.Z[j] -= 1u;
+      }
+      __syncthreads();
+      nZ += 1;
+      Gz = G - 1;
+    }
+  }
+  if (exact)
+    sgn = form_shifted<NT>(s, colrow, p.C, p.mom.sign[mk], p.mom.exp[mk], mlimbs, q.x.sign[0], q.x.exp[0],
+                           q.x.limbs, xz, L, G, p.st, &nZ, &Gz);
   if (sgn == 0) {
     if (threadIdx.x == 0) atomicMin(&p.st->range_row, i);
     return;

@@ -417,8 +417,9 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
   }
   const int nterm = p.sub[sp].nterm;
   for (int k = 0; k < nterm; k++) {
-    const int base = d0 + p.sub[sp].toff[k];
-    const long long sg = p.sub[sp].tsign[k];
+    const int tv = p.sub[sp].term[k];
+    const int base = d0 + (tv >> 1);
+    const long long sg = (tv & 1) ? -1 : 1;
     unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.colsum + crow * p.C + base);
     const int lim = p.C - base;
 #pragma unroll
@@ -794,7 +795,7 @@ cudaError_t launch_wait_selftest(DevStatus *st, long long wait_ns, cudaStream_t 
 
 cudaError_t launch_update(const UpdParams &p, cudaStream_t s) {
   if (p.nout <= 0 || p.t1 <= p.t0 || p.nunits <= 0) return cudaSuccess;
-  if (p.upc % p.uc != 0 || p.nsub < 1 || p.nsub > MAX_SUB || !p.sub) return cudaErrorInvalidValue;
+  if (p.upc % p.uc != 0 || p.nsub < 1 || p.nsub > MAX_SUB) return cudaErrorInvalidValue;
   switch (p.uc) {
     case 7: return launch_uc<7>(p, s);
     case 8: return launch_uc<8>(p, s);
