@@ -119,7 +119,8 @@ int hk_set_update_path(hk_ctx *ctx, int path);
  *   HK_OPT_UPDATE_PATH      0 IMAD product scanning (default), 1 INT8 mma.sync
  *   HK_OPT_KARATSUBA        Karatsuba levels of the IMAD update, 0..4, or -1
  *                           (default): the depth of least modelled update
- *                           cost for the window width
+ *                           cost for the window width (four levels only for
+ *                           N >= 768 and windows of about 580 limbs or more)
  *   HK_OPT_GRAPH            1: capture each factorisation's launch sequence in a
  *                           CUDA graph and replay it (default 0)
  *   HK_OPT_AUTOTUNE         1: choose the update kernel's stripe width and chunk
@@ -389,8 +390,10 @@ int hk_mlp_train(float *params, float *m, float *v, float *grad, const float *x,
  * of the X entries with piece k of the Y entries exactly, and adds that
  * contraction to the result at each of its terms (offset in limbs, sign).
  *   levels     Karatsuba depth 0..4, or -1 for the depth of least modelled
- *              update cost (the hk_factor default); windows below 64 limbs
- *              take at most three levels
+ *              update cost (the hk_factor default for N >= 768; smaller
+ *              factorisations stop at three levels); four levels only where
+ *              three update blocks still fit an SM, and windows below 64
+ *              limbs take at most three
  *   info[9]    out: [0] depth, [1] pieces n, [2] expanded entry stride in
  *              limbs, [3] zero gap between pieces (limbs), [4] stripe width
  *              uc, [5] chunk length upc, [6] units, [7] blocks per output with

@@ -58,7 +58,6 @@ struct Sched {
   int n, uc, upc;
   int nsub;
   SubProb sub[MAX_SUB];
-  KSub ksub[MAX_SUB];  // the kernel's packed copy
   int C;  // column sums per output
   int nxb, maxlen;  // per-block operand windows (Karatsuba), see UpdParams
   int xlo[MAX_XB], xlen[MAX_XB];
@@ -93,6 +92,7 @@ struct hk_ctx {
   KarLayout kl{};
   int kar_levels = -1;       // Karatsuba levels of the factor update (-1: chosen per window)
   int lv_W = -1, lv_auto = 0;  // cached automatic choice for window lv_W
+  bool lv_big = false;         // ... and for a factorisation of at least 768 rows
   int update_path = 0;       // 0: IMAD product scanning, 1: INT8 mma.sync
   bool use_graph = false;    // capture each factorisation in a CUDA graph
   cudaStream_t cap_stream = nullptr;  // capture stream when `stream` is a default stream
@@ -353,7 +353,7 @@ bool autotune_schedule(hk_ctx *c, const SubProb *sub, int nsub, int stride, int 
       up.uc = uc;
       up.upc = upc;
       up.nsub = nsub;
-      for (int k = 0; k < nsub; k++) ok = ok && pack_ksub(sub[k], &up.sub[k]);
+      for (int k = 0; k < nsub; k++) up.sub[k] = sub[k];
       up.r0 = r0;
       up.ra = r0;
       up.rb = r1;
@@ -481,8 +481,6 @@ cudaError_t sched_for(hk_ctx *c, int Wx, int Wy, int levels, Sched *out) {
   plan_units(sp, Wx, Wy, levels, uc, upc, &sc, &h);
   cudaError_t e = alloc(c, c->base_arena, &sc.units, (size_t)sc.n);
   if (e != cudaSuccess) return e;
-  for (int k = 0; k < sc.nsub; k++)
-    if (!pack_ksub(sc.sub[k], &sc.ksub[k])) return cudaErrorInvalidValue;  // offsets beyond the packed range
   // on the context's stream: a plain cudaMemcpy runs on the legacy default
   // stream, which a non-blocking context stream does not wait for, and for
   // pageable memory it returns before the transfer has landed
@@ -499,7 +497,7 @@ void fill_sched(UpdParams &up, const Sched &sc) {
   up.uc = sc.uc;
   up.upc = sc.upc;
   up.nsub = sc.nsub;
-  for (int k = 0; k < sc.nsub; k++) up.sub[k] = sc.ksub[k];
+  for (int k = 0; k < sc.nsub; k++) up.sub[k] = sc.sub[k];
   up.C = sc.C;
   up.nxb = sc.nxb;
   for (int k = 0; k < sc.nxb; k++) {
@@ -558,9 +556,15 @@ cudaError_t ensure_la_streams(hk_ctx *c);
 int factor_levels(hk_ctx *c) {
   if (c->update_path == 1) return 0;
   if (c->kar_levels >= 0) return c->kar_levels;
-  if (c->lv_W != c->W) {
-    c->lv_auto = choose_levels(c->W, KAR_GAP);
+  const bool big = c->N >= 768;
+  if (c->lv_W != c->W || c->lv_big != big) {
+    // four levels only for large factorisations: the expansion of each new
+    // entry into 81 pieces sits on the panel chain (N^2/2 entries) and pays
+    // off against the update's N^3/6 products from about N = 768 (measured at
+    // P = 24576: 2% slower at N = 512, faster at N = 1000)
+    c->lv_auto = choose_levels(c->W, KAR_GAP, big);
     c->lv_W = c->W;
+    c->lv_big = big;
   }
   return c->lv_auto;
 }
@@ -1933,7 +1937,7 @@ int hk_selftest_mp(int op, int L, const uint32_t *x, int nx, int64_t ex, const u
 int hk_update_plan(int W, int levels, int64_t *info, int32_t *splits, int32_t *pieces, int32_t *terms,
                    int32_t *units, int64_t ucap, int32_t *win) {
   if (W < 1 || W > (1 << 20) || levels < -1 || levels > MAX_KAR || !info) return HK_ERR_ARG;
-  const int lv = levels < 0 ? choose_levels(W, KAR_GAP) : levels;
+  const int lv = levels < 0 ? choose_levels(W, KAR_GAP, true) : levels;
   SubPlan sp;
   plan_subprobs(W, W, lv, &sp);
   int uc = 0, upc = 0;

@@ -56,33 +56,6 @@ struct SubProb {
   int tsign[MAX_TERMS];
 };
 
-// The kernel's copy of a sub-contraction, small enough for 81 of them to ride
-// in the launch parameters: piece offsets and each term packed as
-// 2 * offset + (1 if the sign is negative).
-struct KSub {
-  int16_t xoff, yoff, nterm, pad;
-  int16_t term[MAX_TERMS];
-};
-// Packs sub into k; false when an offset does not fit (then the launch is refused).
-inline bool pack_ksub(const SubProb &sub, KSub *k) {
-  if (sub.xoff < 0 || sub.xoff > 32767 || sub.yoff < 0 || sub.yoff > 32767 || sub.nterm < 1 ||
-      sub.nterm > MAX_TERMS)
-    return false;
-  k->xoff = (int16_t)sub.xoff;
-  k->yoff = (int16_t)sub.yoff;
-  k->nterm = (int16_t)sub.nterm;
-  k->pad = 0;
-  for (int t = 0; t < MAX_TERMS; t++) {
-    if (t >= sub.nterm) {
-      k->term[t] = 0;
-      continue;
-    }
-    if (sub.toff[t] < 0 || sub.toff[t] > 16383) return false;
-    k->term[t] = (int16_t)(2 * sub.toff[t] + (sub.tsign[t] < 0 ? 1 : 0));
-  }
-  return true;
-}
-
 // Karatsuba expansion of an aligned entry of W limbs (levels 0 to 4):
 // pieces lo, hi, lo+hi (recursively), each stored in its own slot with zero
 // gaps of G limbs on both sides, so that one entry is one contiguous copy.
@@ -116,7 +89,10 @@ struct UpdParams {
   int uc;                  // stripe width of the unit table (7, 9, 11 or 13)
   int upc;                 // p-steps per unit (a multiple of uc)
   int nsub;
-  KSub sub[MAX_SUB];       // sub-contractions (read through the constant cache)
+  // the sub-contractions, in the launch parameters (about 12 KB at 81 pieces):
+  // the unit loop reads them through the constant cache; a table in device
+  // memory measured 10% slower, one packed into 16-bit fields 12% slower
+  SubProb sub[MAX_SUB];
   int r0;                  // first row of the current block (output indexing)
   int ra, rb;              // output rows [ra, rb)
   int nout;                // number of outputs
@@ -148,7 +124,7 @@ int build_units(const SubProb *sub, int nsub, int uc, int upc, Unit *host_out, i
 int operand_windows(const SubProb *sub, int nsub, const Unit *units, int n, int gap, int stride, int *xlo,
                     int *xlen);
 void choose_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc, int *upc);
-int choose_levels(int W, int gap);  // Karatsuba depth of least modelled update cost
+int choose_levels(int W, int gap, bool allow4);  // Karatsuba depth of least modelled update cost
 int colsum_width(const SubProb *sub, int nsub, int uc);
 cudaError_t launch_update(const UpdParams &p, cudaStream_t s);
 // One block waits (bounded by wait_ns, 0 = default) on an mbarrier that nothing

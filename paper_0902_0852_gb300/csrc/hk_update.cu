@@ -417,9 +417,8 @@ __global__ void __launch_bounds__(UNT + 32, HK_UPDATE_MINBLOCKS) k_update(const 
   }
   const int nterm = p.sub[sp].nterm;
   for (int k = 0; k < nterm; k++) {
-    const int tv = p.sub[sp].term[k];
-    const int base = d0 + (tv >> 1);
-    const long long sg = (tv & 1) ? -1 : 1;
+    const int base = d0 + p.sub[sp].toff[k];
+    const long long sg = p.sub[sp].tsign[k];
     unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.colsum + crow * p.C + base);
     const int lim = p.C - base;
 #pragma unroll
@@ -725,24 +724,43 @@ void choose_schedule(const SubProb *sub, int nsub, int upc_cap, int *uc_out, int
   best_schedule(sub, nsub, upc_cap, uc_out, upc_out);
 }
 
+// Shared memory of one update block for the schedule (uc, upc) of a
+// Karatsuba launch: the default ring of USTAGES stages of the longest block
+// operand window (as launch_uc sizes it).
+static size_t staged_bytes(const SubProb *sub, int nsub, int uc, int upc, const KarLayout &kl) {
+  const int n = build_units(sub, nsub, uc, upc, nullptr, 0);
+  std::vector<Unit> h(n);
+  build_units(sub, nsub, uc, upc, h.data(), n);
+  int xlo[MAX_XB], xlen[MAX_XB];
+  int len = operand_windows(sub, nsub, h.data(), n, kl.G, kl.stride, xlo, xlen);
+  if (len <= 0) len = kl.stride;  // whole entries staged
+  const int Xsz = ((len + xpadr(upc) + 3) / 4) * 4;
+  const int Ysz = ((ypadl(uc, upc) + len + ypadr(uc) + 3) / 4) * 4;
+  return (size_t)USTAGES * (Xsz + Ysz) * 4 + 2 * USTAGES * 8 + 4 * (USTAGES + 4);
+}
+
 // Karatsuba depth for a window of W limbs: the level count whose best
 // schedule has the least modelled cost (the model of choose_schedule, which
 // counts every thread slot of the unit grid, so narrow pieces pay for their
-// idle slots and per-unit overhead), up to MAX_AUTO_KAR levels.  The model
-// does not see the staged operand windows, which grow with the zero gaps of
-// 81 pieces (at W = 300 a four-level block would stage about 114 KB, one
-// block per SM); deeper expansions are taken by option only.
-constexpr int MAX_AUTO_KAR = 3;
-int choose_levels(int W, int gap) {
+// idle slots and per-unit overhead).  The model sees neither the staged
+// operand windows, which grow with the zero gaps between pieces, nor the
+// expansion of every new entry into 81 pieces on the panel chain: four
+// levels are considered only when allowed (large factorisations) and where
+// three update blocks still fit an SM (about W >= 580; at W = 300 a
+// four-level block would stage 114 KB).
+int choose_levels(int W, int gap, bool allow4) {
   int best_lv = 0;
   double best = 1e300;
-  for (int lv = 0; lv <= MAX_AUTO_KAR; lv++) {
+  for (int lv = 0; lv <= MAX_KAR; lv++) {
+    if (lv == 4 && !allow4) break;
     KarLayout kl;
     kar_layout(W, lv, gap, &kl);
+    if (kl.levels != lv) break;
     SubProb sub[MAX_SUB];
     const int nsub = kar_subprobs(kl, sub);
     int uc = 0, upc = 0;
     const double cost = best_schedule(sub, nsub, lv > 0 ? kl.G - 11 : 8 * UC_MAX, &uc, &upc);
+    if (lv == 4 && staged_bytes(sub, nsub, uc, upc, kl) > 72 * 1024) break;
     if (cost < best * 0.98) {  // a deeper level must win by 2% (more expansion work per entry)
       best = cost;
       best_lv = lv;

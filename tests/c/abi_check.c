@@ -14,7 +14,7 @@ int main(void) {
   int64_t info[9];
   int32_t splits[40], pieces[3 * 81], terms[2 * 16 * 81];
   if (hk_update_plan(804, -1, info, splits, pieces, terms, NULL, 0, NULL) != HK_OK) return 4;
-  if (info[0] < 0 || info[0] > 3 || info[1] < 1 || info[6] < 1) return 5;
+  if (info[0] < 0 || info[0] > 4 || info[1] < 1 || info[6] < 1) return 5;
   if (hk_factor(NULL, NULL) != HK_ERR_ARG || hk_smallest_eig(NULL, 1, NULL, NULL) != HK_ERR_ARG) return 6;
   hk_ctx *ctx = NULL;
   if (hk_create(NULL, 0, NULL) != HK_ERR_ARG || ctx != NULL) return 7;

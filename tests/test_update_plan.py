@@ -121,15 +121,19 @@ def test_unit_reads_stay_in_gaps_and_windows(hk, W, levels):
 
 
 def test_automatic_depth_follows_the_cost_model(hk):
-    # three levels once the pieces stay wide enough to fill the unit grid
-    assert hk.hk_update_plan(804, -1, with_units=False)["levels"] == 3
+    # three levels once the pieces stay wide enough to fill the unit grid;
+    # four only where three update blocks still fit an SM with the staged
+    # windows of 81 pieces (the plan assumes a factorisation of at least 768
+    # rows; smaller ones stop at three)
     assert hk.hk_update_plan(400, -1, with_units=False)["levels"] == 3
+    assert hk.hk_update_plan(560, -1, with_units=False)["levels"] == 3
+    assert hk.hk_update_plan(804, -1, with_units=False)["levels"] == 4
     # deeper levels only as the window widens
-    depths = [hk.hk_update_plan(W, -1, with_units=False)["levels"] for W in (8, 40, 100, 176, 300, 400, 804)]
+    depths = [hk.hk_update_plan(W, -1, with_units=False)["levels"] for W in (8, 40, 100, 176, 300, 400, 804, 1100)]
     assert depths == sorted(depths) and depths[0] == 0
     for W in (8, 64, 176, 804, 1200):
         plan = hk.hk_update_plan(W, -1, with_units=False)
-        assert 0 <= plan["levels"] <= 3 and plan["C"] >= 2 * W  # four levels by option only
+        assert 0 <= plan["levels"] <= 4 and plan["C"] >= 2 * W
 
 
 def test_plan_argument_checks(hk):
