@@ -33,7 +33,13 @@ SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.act
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 # DRAM bytes (read + write) per executed limb product of the update kernel, from
 # one ncu capture of the current kernel version; None when not measured.
-UPDATE_TRAFFIC_BYTES_PER_LIMBPROD = (8.395456e9 + 0.0322035e9) / (3976 * 256 * 265833)  # k_update_stripe8_N512_P24576_full.md
+# DRAM bytes (read + write) per executed limb product of the update kernel,
+# by Karatsuba depth, from one ncu capture each of the same launch (rows
+# 256..271 against t < 256 at N = 512, P = 24576)
+UPDATE_TRAFFIC_BYTES_PER_LIMBPROD = {
+    3: (8.395456e9 + 0.0322035e9) / (3976 * 256 * 265833),   # k_update_stripe8_N512_P24576_full.md
+    4: (39.609636e9 + 0.03896192e9) / (3976 * 256 * 202748),  # k_update_karatsuba4_N512_P24576_full.md
+}
 
 
 def parse():
@@ -390,8 +396,8 @@ def main():
     peak = n_sm * 64 * max_mhz * 1e6 / 2 / 1e12
     # per update launch, averaged like `achieved`: one big update per 16-row
     # block after the first plus one in-block update per row -> N - 1 launches
-    traffic = (UPDATE_TRAFFIC_BYTES_PER_LIMBPROD * (N - 1) * N * (N + 1) // 6 * st["limbprod_per_mac"] /
-               (N - 1)) if UPDATE_TRAFFIC_BYTES_PER_LIMBPROD else None
+    per_prod = UPDATE_TRAFFIC_BYTES_PER_LIMBPROD.get(st["karatsuba_levels"])
+    traffic = (per_prod * (N - 1) * N * (N + 1) // 6 * st["limbprod_per_mac"] / (N - 1)) if per_prod else None
     n_lam, e_lam = lam
     # decimal rendering of lambda (n * 2^e) with 10 significant digits
     lg = math.log10(abs(n_lam)) + e_lam * math.log10(2)
