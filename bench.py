@@ -56,7 +56,7 @@ def parse():
                     help="skip the predicted-precision time-to-lambda comparison (after the timed region)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the after-region comparisons (Secant, INT8 update, batched sweep)")
-    ap.add_argument("--paper-cells", default=None, metavar="N:p/q,...|default",
+    ap.add_argument("--paper-cells", default=None, metavar="N:p/q,...|default|all",
                     help="instead of the bench: Table 3 cells at a verified precision, one JSON line")
     return ap.parse_args()
 
@@ -64,10 +64,10 @@ def parse():
 def run_paper_cells(spec):
     """Table 3 cells (N, beta) on the device at a verified precision."""
     from paper_0902_0852_gb300 import build
-    from paper_0902_0852_gb300.paper_cells import DEFAULT_CELLS, run_cell
+    from paper_0902_0852_gb300.paper_cells import ALL_CELLS, DEFAULT_CELLS, run_cell
     build.build()
-    if spec == "default":
-        cells = DEFAULT_CELLS
+    if spec in ("default", "all"):
+        cells = DEFAULT_CELLS if spec == "default" else ALL_CELLS
     else:
         cells = []
         for item in spec.split(","):

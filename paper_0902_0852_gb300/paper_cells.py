@@ -42,6 +42,9 @@ DEFAULT_CELLS = [(500, (1, 3)), (500, (1, 2)), (1000, (1, 3)), (1000, (1, 2)), (
                  (1500, (1, 1)), (1500, (7, 4))]
 
 
+ALL_CELLS = [(N, beta) for N in (100, 300, 500, 1000, 1500) for beta in ((1, 3), (1, 2), (1, 1), (7, 4))]
+
+
 def p_cell(N):
     """Starting precision of a Table 3 cell: 32 ceil((3.5 N + 512) / 32) bits."""
     return 32 * ((7 * N + 1024 + 63) // 64)

@@ -50,3 +50,42 @@ def test_oracle_table3_N100_small_beta(beta, T):
     m = inputs.moments(100, beta, P)
     lam, hist, _ = H.smallest_eigenvalue(m, 100, P, T)
     assert sig5(lam) == TABLE3[(100, beta)]
+
+
+def _fake_solver(value):
+    def solve(N, beta, predictor=None, P=None, T=None, max_escalations=8):
+        return dict(lam=value, P=P, iters=8, tried=[P, P + 1024], seconds=1.0, verified=True, T=T)
+    return solve
+
+
+def test_run_cell_compares_with_table3(monkeypatch):
+    """run_cell passes the cell's starting precision to the verified solve and
+    compares the five-figure rounding of its value with Table 3 (a stand-in
+    solver here: the device runs are the GPU tests and bench.py --paper-cells)."""
+    from paper_0902_0852_gb300 import paper_cells as pc
+    from paper_0902_0852_gb300 import predictor as pr
+    monkeypatch.setattr(pr, "solve_verified", _fake_solver(inputs._round_ratio(33763, 10000, 128)))
+    r = pc.run_cell(500, (1, 3))
+    assert r["P"] == p_cell(500) and r["tried"] == [p_cell(500), p_cell(500) + 1024]
+    assert r["lambda"] == "3.3763e0" and r["table3"] == "3.3763e0" and r["match"] and r["verified"]
+    # the N = 1500, beta = 1/2 cell: the device value against the printed one
+    monkeypatch.setattr(pr, "solve_verified", _fake_solver(inputs._round_ratio(65295, 1000000, 128)))
+    r = pc.run_cell(1500, (1, 2))
+    assert r["lambda"] == "6.5295e-2" and r["table3"] == "6.6295e-2" and not r["match"]
+    # a failed solve reports no value and no match
+    monkeypatch.setattr(pr, "solve_verified", _fake_solver(None))
+    r = pc.run_cell(100, (7, 4))
+    assert r["lambda"] is None and not r["match"]
+
+
+def test_table3_holds_every_cell():
+    assert len(TABLE3) == 20
+    for N in (100, 300, 500, 1000, 1500):
+        for beta in ((1, 3), (1, 2), (1, 1), (7, 4)):
+            d, k = TABLE3[(N, beta)]
+            assert 10 ** 4 <= d < 10 ** 5
+    # lambda_1 decreases with N in every column (Table 3's own monotonicity)
+    for beta in ((1, 3), (1, 2), (1, 1), (7, 4)):
+        vals = [Fraction(TABLE3[(N, beta)][0]) * Fraction(10) ** TABLE3[(N, beta)][1]
+                for N in (100, 300, 500, 1000, 1500)]
+        assert vals == sorted(vals, reverse=True)
