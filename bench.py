@@ -413,7 +413,7 @@ def main():
                    "iters": "converged" if args.iters == 0 else args.iters,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "no flush: working set (R, its aligned copy and their Karatsuba expansion, about "
-                         "12 GB at N=1000) is far larger than L2"},
+                         "22 GB at N=1000) is far larger than L2"},
         "time_to_lambda_s": t_dev / args.steps, "iters_used": used, "lambda_min": lam_str,
         "lambda_min_table3": "1.0892e-52" if (N, P) == (1000, 24576) else None,
         "factor_ms": fac_ms / args.steps, "inverse_iteration_ms": eig_ms / args.steps,
