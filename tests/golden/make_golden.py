@@ -23,6 +23,10 @@ CASES = [
     # the paper-scale factorial matrix: every step of the factorisation is exact
     # at this P, so the oracle's factor is its closed form (cholesky_factorial)
     ("paper_scale_beta1", 1000, (1, 1), 24576, 3),
+    # Table 3 cells whose moments grow fastest (exact factorials 3 (3k+2)! and
+    # 2 (2k+1)!), at the precision the cells run at (32 ceil((3.5 N + 512)/32))
+    ("cell_N500_beta1_3", 500, (1, 3), 2272, 3),
+    ("cell_N500_beta1_2", 500, (1, 2), 2272, 3),
 ]
 
 

@@ -67,3 +67,35 @@ def test_table3_N1500_beta_half_by_inertia():
             assert zero == -1
             counts.append(neg)
     assert counts == [0, 1, 1], counts
+
+
+@pytest.mark.parametrize("name", ["cell_N500_beta1_3", "cell_N500_beta1_2"])
+def test_cell_N500_R_and_history_bit_exact(name):
+    """N = 500, beta = 1/3 and 1/2, P = 2272 (the cells' precision), T = 3
+    steps from the all-ones vector: the digest of R and lambda_1..lambda_3
+    equal the stored oracle values (tests/golden/make_golden.py, written from
+    oracle/ only); the factorisation takes its window widening on the way."""
+    import json
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "golden", f"{name}.json")) as f:
+        g = json.load(f)
+    sys.path.insert(0, os.path.join(here, "golden"))
+    from make_golden import digest_R
+    from paper_0902_0852_gb300 import build, hk
+    build.build()
+    N, P, T, beta = g["N"], g["P"], g["T"], tuple(g["beta"])
+    m = inputs.moments(N, beta, P)
+    with hk.Hankel(0) as h:
+        h.load(N, beta, P, m)
+        h.factor()
+        sign, exp, limbs = hk.hk_get_R_flat(h.ctx, N, P)
+        lam, used = h.smallest_eig(T)
+        hist = h.history(used)
+    vals = hk.unpack(sign, exp, limbs)
+    rows, k = [], 0
+    for t in range(N):
+        rows.append(vals[k:k + N - t])
+        k += N - t
+    assert digest_R(rows, P) == g["R_sha256"]
+    assert used == T
+    assert [[str(n), e] for n, e in hist] == g["history"]
