@@ -42,14 +42,39 @@ def test_inputs_small_beta_are_factorials():
                 assert Fraction(n) * Fraction(2) ** e == exact
 
 
-@pytest.mark.parametrize("beta,T", [((1, 3), 12), ((1, 2), 30)])
-def test_oracle_table3_N100_small_beta(beta, T):
-    """Table 3, N = 100: beta = 1/3 -> 3.4720, beta = 1/2 -> 2.7397e-1 (the
-    oracle converges in 7 and 24 steps from the all-ones vector)."""
-    P = p_cell(100)
-    m = inputs.moments(100, beta, P)
-    lam, hist, _ = H.smallest_eigenvalue(m, 100, P, T)
-    assert sig5(lam) == TABLE3[(100, beta)]
+@pytest.fixture(scope="module")
+def oracle_N100_small_beta():
+    """The oracle's lambda_1 at N = 100 for beta = 1/3 and 1/2 (it converges in
+    7 and 24 steps from the all-ones vector)."""
+    out = {}
+    for beta, T in (((1, 3), 12), ((1, 2), 30)):
+        P = p_cell(100)
+        lam, _, _ = H.smallest_eigenvalue(inputs.moments(100, beta, P), 100, P, T)
+        out[beta] = lam
+    return out
+
+
+@pytest.mark.parametrize("beta", [(1, 3), (1, 2)])
+def test_oracle_table3_N100_small_beta(oracle_N100_small_beta, beta):
+    """Table 3, N = 100: beta = 1/3 -> 3.4720, beta = 1/2 -> 2.7397e-1."""
+    assert sig5(oracle_N100_small_beta[beta]) == TABLE3[(100, beta)]
+
+
+@pytest.mark.parametrize("beta,want", [((1, 3), (852, 1396)), ((1, 2), (736, 861))])
+def test_oracle_table1_N100_small_beta(oracle_N100_small_beta, beta, want):
+    """Table 1's lower bound on cond(M) is Gamma((2N-1)/beta)/beta / lambda_1:
+    at N = 100 it prints 8.52e1396 (beta = 1/3) and 7.36e861 (beta = 1/2).
+    With beta = 1/q the numerator is the integer q (199 q - 1)!; three
+    significant figures computed exactly."""
+    from math import factorial, floor, log10
+    q = beta[1]
+    cond = Fraction(q * factorial(199 * q - 1)) / H.to_fraction(oracle_N100_small_beta[beta])
+    k = floor(log10(cond.numerator) - log10(cond.denominator))
+    d = round(cond / Fraction(10) ** (k - 2))
+    if d >= 1000:  # the float estimate of the exponent was one low
+        k += 1
+        d = round(cond / Fraction(10) ** (k - 2))
+    assert (d, k) == want
 
 
 def _fake_solver(value):
