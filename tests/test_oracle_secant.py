@@ -45,7 +45,8 @@ def test_beta1_pivots_are_factorial_squares(N):
 
 
 @pytest.mark.parametrize("beta,N,P,xfrac", [((7, 4), 8, 256, Fraction(1, 3)), ((3, 4), 6, 192, Fraction(2, 1)),
-                                            ((1, 1), 6, 192, Fraction(5, 2))])
+                                            ((1, 1), 6, 192, Fraction(5, 2)), ((1, 2), 8, 256, Fraction(1, 2)),
+                                            ((1, 3), 8, 256, Fraction(3, 2))])
 def test_det_and_inertia_match_an_exact_determinant(beta, N, P, xfrac):
     """det(M - xI) at a shift below lambda_1 (xfrac < 1) or above it (xfrac > 1):
     the P-bit LDL^T determinant and the exact rational one of the oracle both
@@ -67,7 +68,7 @@ def test_det_and_inertia_match_an_exact_determinant(beta, N, P, xfrac):
 
 
 CASES = [((1, 1), 4, 256), ((7, 4), 4, 256), ((1, 1), 16, 640), ((7, 4), 24, 1024), ((3, 4), 20, 1024),
-         ((3, 2), 12, 512)]
+         ((3, 2), 12, 512), ((1, 2), 16, 640), ((1, 3), 16, 640)]
 
 
 @pytest.mark.parametrize("beta,N,P", CASES)
