@@ -25,7 +25,10 @@ mpmath = pytest.importorskip("mpmath")
 
 def _candidates(x, P):
     """The two P-bit floats around the positive rational x."""
-    e = math.floor(math.log2(x)) - P + 1 if x > 0 else 0
+    # a first guess from the bit lengths (a float log2 would overflow for the
+    # moments of fast-growing weights, beyond 2^1024), off by at most one
+    x = Fraction(x)
+    e = x.numerator.bit_length() - x.denominator.bit_length() - P + 1 if x > 0 else 0
     # fix e so that x / 2**e lies in [2**(P-1), 2**P)
     while x / Fraction(2) ** e >= 2 ** P:
         e += 1
@@ -206,7 +209,8 @@ def _audit(moments, R, P):
 
 
 @pytest.mark.parametrize("beta,N,P", [((1, 1), 24, 256), ((7, 4), 40, 384), ((3, 4), 40, 384),
-                                      ((3, 2), 24, 512), ((2, 1), 17, 320)])
+                                      ((3, 2), 24, 512), ((2, 1), 17, 320), ((1, 2), 30, 384),
+                                      ((1, 3), 30, 384)])
 def test_every_rounding_audited(beta, N, P):
     """The oracle's R, entry by entry, is the once-rounded value its
     definition gives (the same R the device parity tests compare bit for bit)."""
@@ -266,7 +270,8 @@ def _mp_lambda_min(moments, N, prec):
 @pytest.mark.parametrize("beta,N,P,T", [((1, 1), 4, 256, 60), ((7, 4), 4, 256, 60),
                                         ((1, 1), 16, 640, 40), ((7, 4), 12, 512, 40),
                                         ((3, 4), 10, 512, 40), ((7, 4), 32, 1024, 60),
-                                        ((1, 1), 32, 1536, 60), ((3, 4), 24, 1024, 60)])
+                                        ((1, 1), 32, 1536, 60), ((3, 4), 24, 1024, 60),
+                                        ((1, 2), 24, 1024, 60), ((1, 3), 24, 1024, 40)])
 def test_lambda_vs_2P_eigensolve(beta, N, P, T):
     """Relative error of lambda_min against an independent dense symmetric
     eigensolve of the same (rounded-moment) matrix at 2P bits is <= 2^-128."""

@@ -76,7 +76,7 @@ def audit_iteration(R, P, T):
 
 
 CASES = [((1, 1), 24, 256, 4), ((7, 4), 40, 384, 3), ((3, 4), 40, 384, 3), ((3, 2), 20, 320, 4),
-         ((7, 4), 12, 96, 6)]
+         ((7, 4), 12, 96, 6), ((1, 2), 24, 320, 3), ((1, 3), 24, 320, 3)]
 
 
 @pytest.mark.parametrize("beta,N,P,T", CASES)
